@@ -1,0 +1,383 @@
+"""Pins of the FP64 CPU oracle to facts that do not come from the oracle itself.
+
+Each test checks the oracle against something the paper or the mathematics
+fixes: constants printed in the paper (tests/golden/paper_constants.json),
+exact moment identities of Eqs. 10-11, the closed form of the isotropic
+gradient, the closed forms of Eq. 13 and of the psi/tanh identity (Eqs. 5-6),
+global mass conservation (Eq. 8 is in divergence form), the diffusion rate
+M = c_s^2 (tau - 1/2) that the paper states the scheme recovers, discrete
+symmetries of the lattice, and near-stationarity of the Eq. 2 profile.
+A plausible slip anywhere in the oracle (dropped term, wrong sign, wrong index,
+transposed operand) breaks at least one of them.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2203_05230_gb300 import workloads as W
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_constants.json")))
+
+
+def test_lattice_constants_as_printed():
+    w, cx, cy = O.lattice()
+    g = GOLD["d2q9_weights"]
+    assert w[0] == pytest.approx(g["w0"][0] / g["w0"][1], abs=0)
+    assert np.all(w[1:5] == g["w1_4"][0] / g["w1_4"][1])
+    assert np.all(w[5:9] == g["w5_8"][0] / g["w5_8"][1])
+    assert abs(w.sum() - 1.0) < 1e-15
+    # D2Q9 velocity set: the 9 distinct vectors of {-1,0,1}^2, |c|^2 = 0, 1, 2 by weight class
+    vecs = set(zip(cx.tolist(), cy.tolist()))
+    assert vecs == {(a, b) for a in (-1, 0, 1) for b in (-1, 0, 1)}
+    assert np.all(cx[1:5] ** 2 + cy[1:5] ** 2 == 1) and np.all(cx[5:] ** 2 + cy[5:] ** 2 == 2)
+    # lattice isotropy that makes c_s^2 = 1/3 (Section 2.2): sum w c_a c_b = c_s^2 delta_ab
+    cs2 = GOLD["cs2"]["value"][0] / GOLD["cs2"]["value"][1]
+    assert abs((w * cx * cx).sum() - cs2) < 1e-16
+    assert abs((w * cy * cy).sum() - cs2) < 1e-16
+    assert abs((w * cx * cy).sum()) < 1e-16
+    assert O.DELTA == math.exp(GOLD["regulariser"]["ln_value"])
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_feq_moments(seed):
+    """Eq. 10: zeroth moment phi, first moment phi u, second moment c_s^2 phi I."""
+    rng = np.random.default_rng(seed)
+    w, cx, cy = O.lattice()
+    phi, u, v = rng.uniform(-0.2, 1.2), rng.uniform(-0.1, 0.1), rng.uniform(-0.1, 0.1)
+    f = O.feq(phi, u, v)
+    assert abs(f.sum() - phi) < 1e-15
+    assert abs((cx * f).sum() - phi * u) < 1e-16
+    assert abs((cy * f).sum() - phi * v) < 1e-16
+    assert abs((cx * cx * f).sum() - phi / 3) < 1e-15
+    assert abs((cy * cy * f).sum() - phi / 3) < 1e-15
+    assert abs((cx * cy * f).sum()) < 1e-16
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_forcing_moments(seed):
+    """Eq. 11: F_i has zero mass and first moment G (so it adds no mass)."""
+    rng = np.random.default_rng(seed)
+    w, cx, cy = O.lattice()
+    gx, gy = rng.standard_normal(2)
+    F = O.forcing(gx, gy)
+    assert abs(F.sum()) < 1e-15
+    assert abs((cx * F).sum() - gx) < 1e-15
+    assert abs((cy * F).sum() - gy) < 1e-15
+    assert abs((cx * cx * F).sum()) < 1e-15 and abs((cx * cy * F).sum()) < 1e-15
+
+
+@pytest.mark.parametrize("ka,kb", [(1, 0), (0, 2), (3, 1), (2, 5)])
+def test_isotropic_gradient_closed_form(ka, kb):
+    """For chi = sin(a x) sin(b y) on a periodic lattice the D2Q9 isotropic stencil
+    gives d/dx = cos(a x) sin(a) sin(b y) (2 + cos b)/3 and the transposed form
+    for d/dy (hand-derived: the axis neighbours carry 1/3 of the central
+    difference, each diagonal pair 1/12)."""
+    nx, ny = 32, 24
+    a, b = 2 * math.pi * ka / nx, 2 * math.pi * kb / ny
+    y, x = np.mgrid[0:ny, 0:nx].astype(float)
+    chi = np.sin(a * x) * np.sin(b * y)
+    for (xx, yy) in [(0, 0), (5, 7), (31, 23), (17, 3)]:
+        g = O.grad(chi, xx, yy)
+        ex = math.cos(a * xx) * math.sin(a) * math.sin(b * yy) * (2 + math.cos(b)) / 3
+        ey = math.sin(a * xx) * (2 + math.cos(a)) / 3 * math.cos(b * yy) * math.sin(b)
+        assert abs(g[0] - ex) < 1e-14 and abs(g[1] - ey) < 1e-14
+
+
+def test_psi_closed_forms():
+    """Eq. 13 with the clip: psi(1/2) = 0, saturation values in the bulk, odd
+    symmetry about phi = 1/2, and the inverse of Eq. 5 (reading R1)."""
+    eps, d = 1.7, O.DELTA
+    assert O.psi(0.5, eps) == 0.0
+    lo = eps * math.log(d / (1 + d))
+    for phi in (0.0, -0.3, -1e-9):
+        assert O.psi(phi, eps) == pytest.approx(lo, rel=1e-15)
+    for phi in (1.0, 1.2, 1 + 1e-9):
+        assert O.psi(phi, eps) == pytest.approx(-lo, rel=1e-15)
+    for phi in np.linspace(0.01, 0.99, 17):
+        assert O.psi(1 - phi, eps) == pytest.approx(-O.psi(phi, eps), abs=1e-13)
+        # phi = 1 / (1 + exp(-psi/eps)) up to the regulariser
+        ps = O.psi(phi, eps)
+        assert 1 / (1 + math.exp(-ps / eps)) == pytest.approx(phi, abs=1e-8)
+
+
+@pytest.mark.parametrize("phi", [0.0, 1e-12, 0.05, 0.3, 0.5, 0.77, 0.999, 1.0, -0.01, 1.02])
+def test_sharpening_identity(phi):
+    """Eq. 6 under R1: (1/(4 eps))[1 - tanh^2(psi/(2 eps))] = phi_c (1 - phi_c)/eps up to
+    the regulariser; exactly, tanh(psi/(2 eps)) = (2 phi_c - 1)/(1 + 2 delta)."""
+    eps, d = 0.8, O.DELTA
+    pc = min(max(phi, 0.0), 1.0)
+    S = O.sharpen(O.psi(phi, eps), eps)
+    t = (2 * pc - 1) / (1 + 2 * d)
+    # 1 - t^2 cancels in the bulk: both sides carry an absolute error of ~1e-16
+    assert S == pytest.approx((1 - t * t) / (4 * eps), rel=1e-12, abs=1e-15)
+    # the regulariser adds at most (1 - (1 + 2 delta)^-2)/(4 eps) ~ delta/eps
+    assert S == pytest.approx(pc * (1 - pc) / eps, abs=1.01 * d / eps)
+    assert S >= 0.0
+
+
+def test_profile_width_closed_form():
+    """Eq. 2 under R1: int phi(1-phi) ds = eps and int |dphi/ds| ds = 1, so the
+    width estimator sum phi(1-phi) / sum |grad phi| equals eps for a resolved profile."""
+    eps = 3.0
+    s = np.arange(-4000, 4001) * 0.05  # tails below e^-60
+    phi = np.array([O.profile(v, eps) for v in s])
+    num = (phi * (1 - phi)).sum() * 0.05
+    assert num == pytest.approx(eps, rel=1e-6)
+    assert O.profile(0.0, eps) == 0.5
+    # dphi/ds = phi(1-phi)/eps (Eq. 3 under R1)
+    ds = 1e-5
+    for v in (-2.0, 0.3, 4.0):
+        der = (O.profile(v + ds, eps) - O.profile(v - ds, eps)) / (2 * ds)
+        pv = O.profile(v, eps)
+        assert der == pytest.approx(pv * (1 - pv) / eps, rel=1e-8)
+
+
+def test_velocity_eq14():
+    """Eq. 14 with the sign factor (R5): values against libm, time reversal
+    u(T - t) = -u(t), and zero discrete divergence of the continuum field."""
+    p = O.Params(nx=64, ny=64, U0=0.04, T=2000, sign=1.0)
+    for (x, y, t) in [(3, 10, 0.0), (40, 7, 333.0), (63, 63, 1999.0)]:
+        u, v = O.velocity(p, x, y, t)
+        L = 64
+        eu = 0.04 * math.sin(math.pi * x / L) ** 2 * math.sin(2 * math.pi * y / L) * math.cos(math.pi * t / 2000)
+        ev = -0.04 * math.sin(math.pi * y / L) ** 2 * math.sin(2 * math.pi * x / L) * math.cos(math.pi * t / 2000)
+        assert u == pytest.approx(eu, abs=1e-17) and v == pytest.approx(ev, abs=1e-17)
+        u2, v2 = O.velocity(p, x, y, 2000 - t)
+        assert u2 == pytest.approx(-u, abs=1e-17) and v2 == pytest.approx(-v, abs=1e-17)
+    q = O.Params(nx=64, ny=64, U0=0.04, T=2000, sign=-1.0)
+    assert O.velocity(q, 5, 9, 10.0)[0] == pytest.approx(-O.velocity(p, 5, 9, 10.0)[0], abs=0)
+
+
+def _vortex_sim(L=64, eps=1.0, model=O.MODIFIED):
+    v = W.Vortex(L=L, eps=eps, T=2000)
+    p = O.Params(nx=L, ny=L, tau=v.tau, eps=eps, U0=v.U0, T=v.T, sign=v.sign, model=model)
+    return O.Sim(p, v.phi0()), v
+
+
+def test_collision_conserves_mass_per_node_and_globally():
+    """Eq. 9 with sum_i F_i = 0 and sum_i f_i^eq = phi preserves sum_i f_i at every
+    node; streaming permutes; so the global mass is conserved over a full
+    single-vortex period (64^2, T = 2000) up to rounding (bound 1e-12 relative:
+    ~2000 steps x a few ulp)."""
+    s, _ = _vortex_sim()
+    m0 = s.mass()
+    phi0 = s.phi()
+    s.step(1)
+    # per-node: phi(t=1) summed = mass; the per-node sum of f* is phi(0) at the source
+    assert abs(s.mass() - m0) / m0 < 1e-15
+    s.step(1999, threads=O.threads_available())
+    assert abs(s.mass() - m0) / m0 < 1e-12
+    assert np.isfinite(s.phi()).all()
+    # returns close to its initial shape after one period (paper, Section 3)
+    e1 = np.abs(s.phi() - phi0).sum() / np.abs(phi0).sum()
+    assert e1 < 0.1
+
+
+def test_diffusion_rate_is_cs2_tau_minus_half():
+    """The paper states the scheme recovers Eq. 8 with M = c_s^2 (tau - 0.5). With a
+    huge eps the sharpening term vanishes and Eq. 8 is advection-diffusion: a
+    Fourier mode advected by a uniform u along its wave vector decays as
+    exp(-M k^2 t) and moves at speed u. Without the d_t(phi u) term of Eq. 11 (or
+    with its sign flipped) the decay rate would be off by (tau - 1/2) U^2 / M = 3%
+    here; the lattice correction at k = 2 pi / 128 is ~0.1%."""
+    nx, ny, tau, U = 128, 4, 0.8, 0.1
+    M = (tau - 0.5) / 3
+    k = 2 * math.pi / nx
+    x = np.arange(nx)
+    phi0 = np.broadcast_to(0.5 + 0.2 * np.sin(k * x), (ny, nx)).copy()
+    p = O.Params(nx=nx, ny=ny, tau=tau, eps=1e9, vel_kind=O.UNIFORM, ux=U, uy=0.0)
+    s = O.Sim(p, phi0)
+    t0, t1 = 500, 4500
+    s.step(t0)
+    a0 = (s.phi()[0] * np.exp(-1j * k * x)).sum()
+    s.step(t1 - t0)
+    a1 = (s.phi()[0] * np.exp(-1j * k * x)).sum()
+    lam = -math.log(abs(a1) / abs(a0)) / (t1 - t0)
+    assert lam == pytest.approx(M * k * k, rel=2.5e-3)
+    dphase = (np.angle(a1 / a0) + k * U * (t1 - t0)) % (2 * math.pi)
+    dphase = min(dphase, 2 * math.pi - dphase)
+    assert dphase < 2e-3
+
+
+def test_uniform_advection_translates_exactly_by_lattice_shift():
+    """With a uniform velocity every node does the same arithmetic, so shifting the
+    initial field by whole lattice vectors shifts the result bit for bit."""
+    nx, ny = 24, 20
+    phi0 = W.random_smooth_phi(nx, ny, seed=3, eps=1.0)
+    p = O.Params(nx=nx, ny=ny, tau=0.7, eps=1.0, vel_kind=O.UNIFORM, ux=0.03, uy=-0.02)
+    a = O.Sim(p, phi0).step(25)
+    b = O.Sim(p, np.roll(phi0, (5, -7), axis=(0, 1))).step(25)
+    assert np.array_equal(np.roll(a.phi(), (5, -7), axis=(0, 1)), b.phi())
+
+
+def test_flat_interface_ignores_parallel_velocity():
+    """A flat interface phi(y): the u_x-odd parts of Eqs. 10-11 cancel between the
+    populations with opposite c_x, so a uniform velocity parallel to it does not
+    change phi at all (up to rounding)."""
+    nx, ny = 8, 48
+    phi0 = W.slab_phi0(nx, ny, 12.0, 33.5, eps=1.0)
+    p0 = O.Params(nx=nx, ny=ny, tau=0.9, eps=1.0, vel_kind=O.UNIFORM, ux=0.0, uy=0.0)
+    p1 = O.Params(nx=nx, ny=ny, tau=0.9, eps=1.0, vel_kind=O.UNIFORM, ux=0.05, uy=0.0)
+    a = O.Sim(p0, phi0).step(300)
+    b = O.Sim(p1, phi0).step(300)
+    assert np.abs(a.phi() - b.phi()).max() < 1e-13  # 300 steps x a few ulp; a slip gives ~1e-3
+
+
+@pytest.mark.parametrize("model", [O.MODIFIED, O.CONSERVATIVE])
+def test_mirror_and_transpose_symmetry(model):
+    """Reflecting x (and u) or swapping x and y (and u, v) commutes with the step:
+    catches any asymmetric slip in the velocity set, weights or stencil."""
+    nx = ny = 20
+    phi0 = W.random_smooth_phi(nx, ny, seed=7, eps=1.0)
+    p = O.Params(nx=nx, ny=ny, tau=0.75, eps=1.0, vel_kind=O.UNIFORM, ux=0.02, uy=0.01, model=model)
+    base = O.Sim(p, phi0).step(40).phi()
+    # x -> -x (mod nx), u -> -u
+    pm = O.Params(nx=nx, ny=ny, tau=0.75, eps=1.0, vel_kind=O.UNIFORM, ux=-0.02, uy=0.01, model=model)
+    mir = O.Sim(pm, np.roll(phi0[:, ::-1], 1, axis=1)).step(40).phi()
+    assert np.abs(np.roll(mir[:, ::-1], 1, axis=1) - base).max() < 1e-13
+    # x <-> y, (u, v) -> (v, u)
+    pt = O.Params(nx=nx, ny=ny, tau=0.75, eps=1.0, vel_kind=O.UNIFORM, ux=0.01, uy=0.02, model=model)
+    tr = O.Sim(pt, phi0.T.copy()).step(40).phi()
+    assert np.abs(tr.T - base).max() < 1e-13
+
+
+def test_equilibrium_profile_is_nearly_stationary_and_sharpening_has_the_right_sign():
+    """At u = 0 the Eq. 2 profile (reading R1) balances diffusion and sharpening in
+    Eq. 8, so a flat slab barely moves; with the sharpening term switched off
+    (eps -> infinity) the same slab diffuses by sqrt(2 M t), which is far larger."""
+    nx, ny, eps = 4, 64, 1.0
+    phi0 = W.slab_phi0(nx, ny, 16.0, 47.0, eps)
+    p = O.Params(nx=nx, ny=ny, tau=0.8, eps=eps, vel_kind=O.UNIFORM)
+    s = O.Sim(p, phi0).step(3000)
+    dev = np.abs(s.phi() - phi0).max()
+    q = O.Params(nx=nx, ny=ny, tau=0.8, eps=1e9, vel_kind=O.UNIFORM)
+    d = O.Sim(q, phi0).step(3000)
+    dev_diff = np.abs(d.phi() - phi0).max()
+    assert dev < 0.02 and dev_diff > 0.2
+    # converged: the residual per step is tiny and the phi = 1/2 crossings stay put
+    ph = s.phi()
+    s2 = s.copy().step(1)
+    assert np.abs(s2.phi() - ph).max() < 1e-7
+    col = ph[:, 0]
+    k = int(np.argmax(col > 0.5))
+    ycross = k - 1 + (0.5 - col[k - 1]) / (col[k] - col[k - 1])
+    assert abs(ycross - 16.0) < 2e-2
+
+
+def test_step_cells_matches_full_step():
+    """The sampled-node evaluator (used at full lattice sizes) returns exactly the
+    full step's values at the sampled nodes, on a vortex state mid-run."""
+    s, _ = _vortex_sim(L=32)
+    s.step(7)
+    rng = np.random.default_rng(0)
+    xs = rng.integers(0, 32, 40)
+    ys = rng.integers(0, 32, 40)
+    xs[:4] = [0, 31, 0, 31]
+    ys[:4] = [0, 0, 31, 31]
+    fn, ph = s.step_cells(xs, ys)
+    phi_t = s.phi()
+    nxt = s.copy().step(1)
+    for j in range(len(xs)):
+        assert ph[j] == phi_t[ys[j], xs[j]]
+        assert np.array_equal(fn[j], nxt.f[:, ys[j], xs[j]])
+
+
+def test_conservative_ablation_differs_only_through_normal_and_sharpening():
+    """Eq. 1 (R8) against Eq. 8: identical mass, and identical evolution when the
+    sharpening is switched off (eps -> infinity), since then only advection-diffusion remains."""
+    nx = ny = 16
+    phi0 = W.random_smooth_phi(nx, ny, seed=1, eps=1.0)
+    kw = dict(nx=nx, ny=ny, tau=0.8, eps=1e12, vel_kind=O.UNIFORM, ux=0.01, uy=0.02)
+    a = O.Sim(O.Params(model=O.MODIFIED, **kw), phi0).step(30).phi()
+    b = O.Sim(O.Params(model=O.CONSERVATIVE, **kw), phi0).step(30).phi()
+    assert np.abs(a - b).max() < 1e-9
+    kw["eps"] = 1.0
+    a = O.Sim(O.Params(model=O.MODIFIED, **kw), phi0).step(30)
+    b = O.Sim(O.Params(model=O.CONSERVATIVE, **kw), phi0).step(30)
+    assert abs(a.mass() - b.mass()) < 1e-12 * a.mass()
+    assert np.abs(a.phi() - b.phi()).max() > 1e-4
+
+
+def _moments_after_one_step(s):
+    """Post-collision populations of the state's nodes, recovered by undoing the
+    streaming of one oracle step: f*_i(x) = f_i(x + c_i, t + 1)."""
+    w, cx, cy = O.lattice()
+    nxt = s.copy().step(1)
+    fstar = np.stack([np.roll(nxt.f[i], (-cy[i], -cx[i]), axis=(0, 1)) for i in range(9)])
+    return fstar, cx, cy
+
+
+@pytest.mark.parametrize("t", [0, 37])
+def test_forcing_first_moment_carries_the_explicit_euler_time_derivative(t):
+    """With phi uniform, grad psi = 0 so n = 0 and the bracket of Eq. 11 is just
+    d_t(phi u) = phi(t) u(t) - phi(t-1) u(t-1) (explicit Euler). Taking the first
+    moment of Eq. 9 with Eqs. 10-11: sum c f* = (1 - 1/tau) sum c f + phi u / tau
+    + (1 - 1/(2 tau)) d_t(phi u). The velocity is Eq. 14 evaluated here with libm,
+    at the step index t and t - 1 (readings R4, R5); the derivative is zero at t = 0 (R3)."""
+    L, tau, T = 16, 0.7, 100.0
+    p = O.Params(nx=L, ny=L, tau=tau, eps=1.0, U0=0.05, T=T, sign=1.0)
+    rng = np.random.default_rng(4)
+    phi, phi_prev = 0.75, 0.65
+    w, cx, cy = O.lattice()
+    # dyadic populations summing exactly to phi at every node, so psi is exactly
+    # uniform and grad psi = 0 exactly (the regulariser then gives n = 0)
+    q = 2.0 ** -24
+    f = np.round((w[:, None, None] * phi + rng.standard_normal((9, L, L)) * 1e-3) / q) * q
+    f[0] = phi - f[1:].sum(0)
+    assert np.all(f.sum(0) == phi)
+    s = O.Sim.from_state(p, f, np.full((L, L), phi_prev), t)
+    fstar, cx, cy = _moments_after_one_step(s)
+    y, x = np.mgrid[0:L, 0:L].astype(float)
+
+    def vel(tt):
+        c = math.cos(math.pi * tt / T)
+        return (0.05 * np.sin(np.pi * x / L) ** 2 * np.sin(2 * np.pi * y / L) * c,
+                -0.05 * np.sin(np.pi * y / L) ** 2 * np.sin(2 * np.pi * x / L) * c)
+    u1, v1 = vel(t)
+    u0, v0 = vel(t - 1)
+    for c, uu1, uu0 in ((cx, u1, u0), (cy, v1, v0)):
+        m1f = (c[:, None, None] * f).sum(0)
+        dt_phiu = (phi * uu1 - phi_prev * uu0) if t > 0 else 0.0  # R3: none at the first step
+        expect = (1 - 1 / tau) * m1f + phi * uu1 / tau + (1 - 0.5 / tau) * dt_phiu
+        got = (c[:, None, None] * fstar).sum(0)
+        assert np.abs(got - expect).max() < 1e-15
+    assert np.abs(fstar.sum(0) - phi).max() < 1e-15
+
+
+def test_forcing_first_moment_carries_the_sharpening_flux():
+    """For a flat profile phi(y) at u = 0 the first moment of Eq. 11's bracket is
+    c_s^2 S n with n = (0, +-1) |g|/(|g| + delta) (Eq. 13), g the central difference
+    of psi along y (what the isotropic stencil reduces to for a y-only field), and
+    S = (1 - ((2 phi_c - 1)/(1 + 2 delta))^2)/(4 eps) (the rational form of Eq. 6)."""
+    nx, ny, tau, eps = 4, 40, 0.9, 1.3
+    phi0 = W.slab_phi0(nx, ny, 10.0, 29.5, eps)
+    p = O.Params(nx=nx, ny=ny, tau=tau, eps=eps, vel_kind=O.UNIFORM)
+    s = O.Sim(p, phi0)  # t = 0: no time-derivative term (reading R3)
+    fstar, cx, cy = _moments_after_one_step(s)
+    phi = s.phi()[:, 0]
+    d = O.DELTA
+    pc = np.clip(phi, 0, 1)
+    psi = eps * np.log((pc + d) / (1 - pc + d))
+    g = (np.roll(psi, -1) - np.roll(psi, 1)) / 2
+    n_y = g / (np.abs(g) + d)
+    S = (1 - ((2 * pc - 1) / (1 + 2 * d)) ** 2) / (4 * eps)
+    m1y = (cy[:, None] * s.f[:, :, 0]).sum(0)
+    G = ((cy[:, None] * fstar[:, :, 0]).sum(0) - (1 - 1 / tau) * m1y) / (1 - 0.5 / tau)
+    assert np.abs(G - S * n_y / 3).max() < 1e-15
+    Gx = ((cx[:, None] * fstar[:, :, 0]).sum(0) - (1 - 1 / tau) * (cx[:, None] * s.f[:, :, 0]).sum(0))
+    assert np.abs(Gx).max() < 1e-16
+
+
+def test_vortex64_regression_against_stored_oracle_result():
+    """Guards the oracle against unintended edits: the stored numbers were written
+    by tests/golden/make_golden.py from the oracle alone."""
+    import tests.golden.make_golden as mg
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "oracle_vortex64.json")))
+    now = mg.vortex64()
+    for k in ("E1", "E2", "phi_min", "phi_max"):
+        assert now[k] == pytest.approx(gold[k], rel=1e-9, abs=1e-15)
+    assert abs(now["mass_drift_rel"]) < 1e-12
