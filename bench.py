@@ -1,0 +1,336 @@
+#!/usr/bin/env python3
+"""Benchmark of the fused lattice Boltzmann step (modified conservative ACE, D2Q9).
+
+Workload: the single-vortex benchmark (Section 3, Eq. 14) on a periodic
+2048 x 2048 lattice, FP32 populations, eps 1, tau 0.8, U0 0.04, T = 16 L steps,
+disk R = 0.15 L at (0.5 L, 0.75 L). One bench step is one lattice time step (one
+launch of the fused step kernel). Its working set (2 x 151 MB population
+buffers + a 16.8 MB phi plane) is larger than the 126 MB L2, so no flush is
+needed between steps.
+
+Prints one JSON line. ``--impl reference`` times the FP64 CPU oracle instead (on
+the host cores, a bounded sample per step). Under torchrun each rank runs an
+independent replica of the workload on its own GPU (no collective on the data
+path); the line reports the aggregate over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS"
+BYTES_PER_LUP = {"f64": 160, "f32": 80}
+L2_NOTE = "inputs larger than L2: 2 x 151 MB FP32 population buffers + 16.8 MB phi plane"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--L", type=int, default=2048)
+    ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--rows", type=int, default=0, help="rows per CTA (0: library default)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def workload(args):
+    from paper_2203_05230_gb300 import workloads as W
+    v = W.vortex_fp32(args.L)
+    return v, {
+        "workload": f"single vortex {args.L}x{args.L} {args.precision.upper()} eps {v.eps} tau {v.tau} "
+                    f"U0 {v.U0} T {v.T} steps, disk R {v.R:g} at ({v.xc:g}, {v.yc:g})",
+        "lattice": [args.L, args.L], "T_period": v.T, "eps": v.eps, "tau": v.tau, "U0": v.U0,
+        "l2": L2_NOTE,
+    }
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (SM clock, throttle reasons)."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.lines = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "100",
+                 "-i", str(self.idx)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[3:7]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def rejected(clk):
+    bad = {"hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"}
+    if bad & set(clk.get("reasons", [])):
+        return True
+    if clk.get("sm_mhz") and clk.get("sm_max_mhz") and clk["sm_mhz"] < 0.6 * clk["sm_max_mhz"] \
+            and "sw_power_cap" not in clk["reasons"]:
+        return True
+    return False
+
+
+def stored_traffic(precision: str, L: int):
+    """DRAM bytes per launch of the fused step from the committed ncu summary, or None
+    when the kernel source has changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", f"ace_step_{precision}_{L}.json")
+    if not os.path.exists(path):
+        return None
+    d = json.load(open(path))
+    src = os.path.join(ROOT, "paper_2203_05230_gb300", "csrc", "ace_kernels.cuh")
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if d.get("kernel_source_sha256_16") != h:
+        return None
+    return d.get("dram_bytes_per_launch")
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def cpu_baseline(args, v, seconds):
+    """The FP64 oracle, as it stands, on all host cores: whole-lattice steps of the
+    same workload from t = 0 for about `seconds` of CPU work."""
+    import oracle as O
+    th = O.threads_available()
+    p = O.Params(nx=args.L, ny=args.L, tau=v.tau, eps=v.eps, U0=v.U0, T=v.T, sign=v.sign)
+    s = O.Sim(p, v.phi0())
+    t0 = time.perf_counter()
+    s.step(1, threads=th)
+    one = time.perf_counter() - t0
+    n = max(1, min(2000, int(seconds / max(one, 1e-6))))
+    t0 = time.perf_counter()
+    s.step(n, threads=th)
+    dt = time.perf_counter() - t0
+    return {"value": args.L * args.L * n / dt / 1e6, "unit": METRIC, "cores": th, "kind": "oracle",
+            "sample": f"{n} whole-lattice FP64 oracle steps of the {args.L}x{args.L} vortex from t=1, "
+                      f"{th} OpenMP threads, {dt:.1f} s"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_setup()
+    if rank != 0:
+        return 0
+    import oracle as O
+    v, cfg = workload(args)
+    th = O.threads_available()
+    budget = 100.0  # seconds for the whole --steps K --warmup W run
+    # calibrate: rate of one step on a 64-row periodic strip of the lattice
+    h = 64
+    mk = lambda hh: O.Sim(O.Params(nx=args.L, ny=hh, tau=v.tau, eps=v.eps, U0=v.U0, T=v.T, sign=v.sign),
+                          v.phi0()[:hh])
+    s = mk(h)
+    t0 = time.perf_counter()
+    s.step(2, threads=th)
+    rate = 2 * args.L * h / (time.perf_counter() - t0)
+    per = budget / (args.steps + args.warmup)
+    h = int(max(3, min(args.L, per * rate / args.L)))
+    s = mk(h)
+    s.step(args.warmup, threads=th)
+    t0 = time.perf_counter()
+    s.step(args.steps, threads=th)
+    dt = time.perf_counter() - t0
+    val = args.L * h * args.steps / dt / 1e6
+    line = {"metric": METRIC, "value": val, "unit": METRIC, "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": cfg,
+            "cpu_baseline": {"value": val, "unit": METRIC, "cores": th, "kind": "oracle",
+                             "sample": f"each step: one FP64 oracle step of a {args.L}x{h} periodic strip "
+                                       f"of the vortex lattice (bounded sample), {th} OpenMP threads"},
+            "e2e": {"value": val, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_setup()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    from paper_2203_05230_gb300 import lbm_ace as A
+    v, cfg = workload(args)
+    prec = {"f32": A.F32, "f64": A.F64}[args.precision]
+    stream = torch.cuda.current_stream()
+    lat = A.vortex_lattice(args.L, eps=v.eps, tau=v.tau, U0=v.U0, T=v.T, precision=prec,
+                           stream=stream.cuda_stream, device=dev, rows_per_cta=args.rows)
+    shape = lat.launch_shape()
+    for _ in range(args.warmup):
+        lat.step(1)
+    torch.cuda.synchronize()
+    m0 = lat.mass()
+
+    def timed():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lat.step(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+        return e0.elapsed_time(e1) / 1e3
+
+    with ClockSampler(dev) as cs:
+        secs = timed()
+    clk = cs.summary()
+    note = None
+    if rejected(clk):
+        with ClockSampler(dev) as cs:
+            secs = timed()
+        note = f"first measurement rejected for clocks {clk}; re-measured"
+        clk = cs.summary()
+    m1 = lat.mass()
+    if ws > 1:
+        t = torch.tensor([secs], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        secs = float(t.item())
+    lups = args.L * args.L * args.steps
+    value = ws * lups / secs / 1e6
+    per_launch = secs / args.steps
+    bpl = BYTES_PER_LUP[args.precision] * args.L * args.L
+    peak, peak_kind = measured_peak()
+    achieved = bpl / per_launch / 1e9
+    traffic = stored_traffic(args.precision, args.L)
+    lat.close()
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, v, prec, stream, dev, A)
+
+    line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": per_launch * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+            "config": {**cfg, "launch": {"tile_x": shape[0], "rows_per_cta": shape[1],
+                                         "grid": [shape[2], shape[3]]},
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+                         else "fallback",
+                         "algorithmic_bytes_per_launch": bpl, "kernel": "lbmace::ace_step"},
+            "hbm_gbs_algorithmic": achieved,
+            "mass_drift_rel_timed": (m1 - m0) / m0,
+            "clocks": clk, "gpu_launches": args.steps, "e2e": e2e}
+    if note:
+        line["clock_note"] = note
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args, v, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def run_e2e(args, v, prec, stream, dev, A):
+    """The same metric through the public API with host buffers: phi0 uploaded from
+    pinned host memory, K steps, phi and the mass read back; wall clock."""
+    import torch
+    from paper_2203_05230_gb300 import workloads as W
+    n = args.L * args.L
+    phi0 = torch.from_numpy(v.phi0()).pin_memory()
+    out = torch.empty(n, dtype=torch.float64).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lat = A.Lattice(nx=args.L, ny=args.L, tau=v.tau, eps=v.eps, U0=v.U0, T_period=float(v.T),
+                    vortex_sign=v.sign, precision=prec, stream=stream.cuda_stream, device=dev,
+                    phi0=phi0.numpy(), rows_per_cta=args.rows)
+    lat.step(args.steps)
+    lat.phi(out.numpy().reshape(args.L, args.L))
+    m = lat.mass()
+    dt = time.perf_counter() - t0
+    lat.close()
+    assert math.isfinite(m)
+    return {"value": n * args.steps / dt / 1e6, "unit": METRIC,
+            "h2d_bytes_per_step": 8 * n / args.steps, "d2h_bytes_per_step": (8 * n + 8) / args.steps,
+            "what": "init from pinned host phi0 + K steps + phi and mass read back, wall clock; "
+                    "bytes per step are the run's totals / K"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,179 @@
+/*
+ * lbm_ace.h -- C ABI of the GB300 (sm_103a) lattice Boltzmann solver for the
+ * modified conservative Allen-Cahn equation of H. Liang, "An accurate lattice
+ * Boltzmann method for interface capturing" (arXiv 2203.05230).
+ *
+ * The library advances a phase field phi on a periodic nx x ny D2Q9 lattice
+ * with the BGK equation plus forcing of Eq. 9, the equilibrium of Eq. 10, the
+ * forcing of Eq. 11 and the moment of Eq. 12, computing psi and the unit
+ * normal with the regularisation and the phi clip of Eq. 13, so that the
+ * scheme recovers Eq. 8 with mobility M = c_s^2 (tau - 1/2). The prescribed
+ * velocity is the time-reversed single vortex of Eq. 14 (Section 3), a
+ * uniform velocity, a static field, or a host callback.
+ *
+ * Conventions for every function:
+ *  - The return value is a status (LBM_ACE_OK = 0, negative on error). No
+ *    function aborts or exits; on error a message is available through
+ *    lbm_ace_last_error(ctx) (or lbm_ace_last_error(NULL) when no context
+ *    exists yet). Messages are owned by the library and stay valid until the
+ *    next call on the same context (or, for NULL, on the same thread).
+ *  - Host pointers are owned by the caller and are only read or written
+ *    during the call. The context owns its device memory.
+ *  - All device work is issued on the stream given at init. lbm_ace_step and
+ *    lbm_ace_step_async return without waiting; the functions that return
+ *    values to the host synchronise that stream first.
+ *  - Arrays are row-major: a scalar field is [ny][nx] with x fastest; a
+ *    population field is [9][ny][nx] in the D2Q9 order c_0 = (0,0),
+ *    c_1..c_4 = (1,0), (0,1), (-1,0), (0,-1), c_5..c_8 = (1,1), (-1,1),
+ *    (-1,-1), (1,-1). Node (x, y) sits at integer coordinates.
+ *
+ * Readings of the paper built into the library (where it is silent or
+ * inconsistent):
+ *  - Interface parameter. Eq. 5's middle form disagrees with Eq. 13 by a
+ *    factor 4. The library takes eps as printed in Eq. 13,
+ *    psi = eps ln((phi_c + delta) / (1 - phi_c + delta)), so the equilibrium
+ *    profile of Eq. 2 is phi = 1/2 + 1/2 tanh(s / (2 eps)) and the sharpening
+ *    magnitude of Eqs. 6, 11 is (1/(4 eps)) [1 - tanh^2(psi / (2 eps))]
+ *    = phi_c (1 - phi_c) / eps (up to delta). The paper's eps is 4x this one.
+ *  - Gradient: the D2Q9 isotropic stencil, grad chi = sum_i w_i c_i chi(x + c_i) / c_s^2.
+ *  - Time derivative d_t(phi u) (Section 2.2, "explicit Euler"): the backward
+ *    difference phi(t) u(t) - phi(t-1) u(t-1); zero at the first step t = 0.
+ *  - Initial populations: f_i = f_i^eq(phi0, u(x, 0)); phi(-1) = phi0.
+ */
+#ifndef LBM_ACE_H
+#define LBM_ACE_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+enum {
+    LBM_ACE_OK = 0,
+    LBM_ACE_EINVAL = -1,   /* invalid argument or parameter */
+    LBM_ACE_ENOMEM = -2,   /* device or host allocation failed */
+    LBM_ACE_ECUDA = -3,    /* a CUDA runtime call failed (message has the CUDA error) */
+    LBM_ACE_ENUMERIC = -4, /* non-finite values found by a numeric check */
+    LBM_ACE_ETIMEOUT = -5, /* a bounded device-side wait gave up */
+    LBM_ACE_ECALLBACK = -6 /* the host velocity callback returned non-zero */
+};
+
+/* Storage and arithmetic of the populations. */
+enum {
+    LBM_ACE_F64 = 0,    /* FP64 populations, FP64 arithmetic */
+    LBM_ACE_F32 = 1,    /* FP32 populations, FP32 arithmetic, FP64 mass sums */
+    LBM_ACE_F16DEV = 2, /* populations stored as FP16 deviations f_i - w_i phi, FP32 arithmetic */
+    LBM_ACE_BF16DEV = 3 /* as above with BF16 storage */
+};
+
+/* Interface model. */
+enum {
+    LBM_ACE_MODEL_MODIFIED = 0,    /* the paper's model: Eq. 8 via psi (Eqs. 11, 13) */
+    LBM_ACE_MODEL_CONSERVATIVE = 1 /* ablation: conservative ACE of Eq. 1, normal and
+                                      sharpening from phi itself (S = phi(1-phi)/eps) */
+};
+
+/* Prescribed velocity. */
+enum {
+    LBM_ACE_VEL_SINGLE_VORTEX = 0, /* Eq. 14, see vortex_sign */
+    LBM_ACE_VEL_UNIFORM = 1,       /* (ux, uy) everywhere, all times */
+    LBM_ACE_VEL_FIELD = 2,         /* static field u_field, v_field, all times */
+    LBM_ACE_VEL_CALLBACK = 3       /* vel_fn called on the host once per step */
+};
+
+/* Host velocity callback: fill u and v ([ny][nx], host memory owned by the
+ * library, valid during the call) with the velocity at time t (in steps).
+ * Return 0 on success; any other value stops lbm_ace_step with
+ * LBM_ACE_ECALLBACK. */
+typedef int (*lbm_ace_velocity_fn)(double t, int nx, int ny, double* u, double* v, void* user);
+
+typedef struct lbm_ace_params {
+    int nx, ny;        /* periodic lattice, each >= 3 (Section 3: L x L) */
+    double tau;        /* BGK relaxation time of Eq. 9, > 0.5 */
+    double M;          /* mobility; must equal (tau - 0.5)/3 within 1e-12 relative
+                          (Section 2.2: M = c_s^2 (tau - 0.5) delta_t), or < 0 to derive it */
+    double eps;        /* interface parameter, > 0, convention of the header comment */
+    double reg_delta;  /* regulariser of Eq. 13; 0 selects the paper's e^-20 */
+    int precision;     /* LBM_ACE_F64 .. LBM_ACE_BF16DEV */
+    int model;         /* LBM_ACE_MODEL_* */
+    int velocity_kind; /* LBM_ACE_VEL_* */
+    /* single vortex (Eq. 14): u = s U0 sin^2(pi x/nx) sin(2 pi y/ny) cos(pi t/T),
+       v = -s U0 sin^2(pi y/ny) sin(2 pi x/nx) cos(pi t/T), s = vortex_sign
+       (+1: the sign printed in Eq. 14; -1: the mirror image) */
+    double U0, T_period, vortex_sign;
+    double ux, uy;                 /* LBM_ACE_VEL_UNIFORM */
+    const double* u_field;         /* LBM_ACE_VEL_FIELD: host [ny][nx], copied at init */
+    const double* v_field;
+    lbm_ace_velocity_fn vel_fn;    /* LBM_ACE_VEL_CALLBACK */
+    void* vel_user;
+    const double* phi0;  /* host [ny][nx] initial phi, copied at init; NULL selects the
+                            disk phi0 = 1/2 (1 + tanh((R - r) / (2 eps))) about (xc, yc) */
+    double xc, yc, R;
+    int device;          /* CUDA device ordinal */
+    void* stream;        /* cudaStream_t for all device work; NULL = the legacy default stream */
+    int rows_per_cta;    /* launch shape of the fused step: rows each CTA marches over;
+                            0 selects a default for the lattice size and the device */
+} lbm_ace_params;
+
+typedef struct lbm_ace_ctx lbm_ace_ctx; /* opaque; owns its device buffers */
+
+/* Fill *p with defaults: 64 x 64, tau 0.8, M derived, eps 1, delta e^-20, FP64,
+ * the paper's model, single vortex with U0 0.04, T 2000, sign -1, disk R 9.6 at
+ * (32, 48), device 0, default stream. */
+int lbm_ace_params_default(lbm_ace_params* p);
+
+/* Validate *p, allocate device state and initialise it (f_i = f_i^eq(phi0,
+ * u(x, 0)), t = 0). Checks: nx, ny >= 3; tau > 0.5; eps > 0; M consistent; phi0
+ * finite; the velocity source present. On success *out owns the context. */
+int lbm_ace_init(const lbm_ace_params* p, lbm_ace_ctx** out);
+
+/* Advance n >= 0 steps (Eq. 9, one fused kernel per step). Asynchronous on the
+ * context's stream, except that the callback velocity mode calls the host
+ * function each step. */
+int lbm_ace_step(lbm_ace_ctx* c, long long n);
+
+/* phi(x, t) = sum_i f_i(x, t) (Eq. 12) at the current time t, written to the
+ * host array out[count], count == nx*ny. Synchronous. */
+int lbm_ace_get_phi(lbm_ace_ctx* c, double* out, size_t count);
+
+/* Global mass sum_x sum_i f_i(x, t) of the current state, summed on the
+ * device in FP64 with compensation in a fixed order (deterministic).
+ * Synchronous. Returns LBM_ACE_ENUMERIC (with *out set) when it is not finite. */
+int lbm_ace_mass(lbm_ace_ctx* c, double* out);
+
+/* Global mass sum_x phi(x, t-1) as reduced block by block inside the last
+ * fused step (FP64 block partials, compensated final sum). Synchronous.
+ * LBM_ACE_EINVAL before the first step. */
+int lbm_ace_step_mass(lbm_ace_ctx* c, double* out);
+
+/* Checkpoint: f[9*nx*ny] receives f_i(x, t) (after streaming, as in Eq. 9's
+ * left side), phi_prev[nx*ny] receives phi(x, t-1); either may be NULL.
+ * Synchronous. FP16/BF16 deviation storage is expanded to FP64. */
+int lbm_ace_get_state(lbm_ace_ctx* c, double* f, double* phi_prev);
+
+/* Restore a state written by lbm_ace_get_state (or any state in that layout) at
+ * time t >= 0. Values are rounded to the context's storage precision. */
+int lbm_ace_set_state(lbm_ace_ctx* c, const double* f, const double* phi_prev, long long t);
+
+/* Current time t (number of steps taken since init, or as set). */
+long long lbm_ace_steps_done(const lbm_ace_ctx* c);
+
+/* Rows per CTA chosen for the fused step (the launch shape). */
+int lbm_ace_launch_shape(const lbm_ace_ctx* c, int* tile_x, int* rows_per_cta, int* grid_x, int* grid_y);
+
+/* Block until all device work of the context has finished. */
+int lbm_ace_synchronize(lbm_ace_ctx* c);
+
+const char* lbm_ace_last_error(const lbm_ace_ctx* c);
+const char* lbm_ace_status_string(int status);
+
+/* Free the context and its device memory. NULL is accepted. */
+void lbm_ace_destroy(lbm_ace_ctx* c);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_ACE_H */

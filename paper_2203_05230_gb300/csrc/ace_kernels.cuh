@@ -1,0 +1,402 @@
+// ace_kernels.cuh -- device code of the GB300 (sm_103a) lattice Boltzmann step for
+// the modified conservative Allen-Cahn equation (Liang, arXiv 2203.05230).
+//
+// One fused kernel per time step (ace_step) does, for every node of its tile:
+//   a1 pull-stream        f_i(x, t) = f*_i(x - c_i, t - 1)             (Eq. 9, periodic)
+//   a2 moment             phi = sum_i f_i                               (Eq. 12)
+//   a3 signed distance    psi = eps ln((phi_c + d)/(1 - phi_c + d))     (Eq. 13, clip)
+//   a4 isotropic gradient grad psi = sum_i w_i c_i psi(x + c_i) / c_s^2
+//   a5 normal             n = grad psi / (|grad psi| + d)               (Eq. 13)
+//   a6 sharpening         S = (1/(4 eps)) (1 - tanh^2(psi/(2 eps)))     (Eqs. 6, 11)
+//                           evaluated as (1 - ((2 phi_c - 1)/(1 + 2 d))^2)/(4 eps),
+//                           an exact rewrite since tanh(psi/(2 eps)) = (2 phi_c - 1)/(1 + 2 d)
+//   a7 velocity           Eq. 14 from separable 1-D tables (no memory traffic per node)
+//   a8 time derivative    d_t(phi u) = phi(t) u(t) - phi(t-1) u(t-1)   (explicit Euler)
+//   a9 forcing            F_i = w_i c_i . (d_t(phi u) + c_s^2 S n) / c_s^2   (Eq. 11)
+//   a10 equilibrium       f_i^eq = w_i phi (1 + c_i . u / c_s^2)       (Eq. 10)
+//   a11 collision         f*_i = f_i - (f_i - f_i^eq)/tau + (1 - 1/(2 tau)) F_i  (Eq. 9)
+//   a12 store             f*_i (SoA planes) and phi(t) (becomes phi(t-1) of the next step)
+//   a13 mass partial      one FP64 sum of phi per CTA
+//
+// Data layout in HBM: populations are 9 SoA planes [9][ny][nx] (x fastest) in two
+// ping-pong buffers holding post-collision values f*(t-1); the phi plane [ny][nx]
+// holds phi(t-1) and is overwritten in place with phi(t) by the thread that reads it.
+//
+// Tiling: a CTA owns TILE_X consecutive columns (one per thread) and marches down
+// `rows` rows. For each row r it pulls the 9 populations, forms phi and psi, and
+// keeps psi in a 4-slot shared-memory ring of rows; the collision of row r - 1 runs
+// once psi of rows r - 2 .. r is there. psi at the two columns left and right of
+// the strip (the stencil's halo) is recomputed from the populations by lanes of
+// warp 0, and the strip recomputes psi on one row above and below its range.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbmace {
+
+constexpr int TILE_X = 128;
+
+// D2Q9 velocity set and weights (Section 2.2, after Eq. 10):
+// 0:(0,0) 1:(1,0) 2:(0,1) 3:(-1,0) 4:(0,-1) 5:(1,1) 6:(-1,1) 7:(-1,-1) 8:(1,-1)
+__host__ __device__ constexpr int cx_of(int i)
+{
+    return (i == 1 || i == 5 || i == 8) ? 1 : ((i == 3 || i == 6 || i == 7) ? -1 : 0);
+}
+__host__ __device__ constexpr int cy_of(int i)
+{
+    return (i == 2 || i == 5 || i == 6) ? 1 : ((i == 4 || i == 7 || i == 8) ? -1 : 0);
+}
+template <typename T>
+__host__ __device__ constexpr T w_of(int i)
+{
+    return i == 0 ? T(4) / T(9) : (i < 5 ? T(1) / T(9) : T(1) / T(36));
+}
+
+__device__ __forceinline__ float dlog(float v) { return logf(v); }
+__device__ __forceinline__ double dlog(double v) { return log(v); }
+__device__ __forceinline__ float dsqrt(float v) { return sqrtf(v); }
+__device__ __forceinline__ double dsqrt(double v) { return sqrt(v); }
+
+__device__ __forceinline__ int wrap_idx(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
+
+enum { MODEL_MODIFIED = 0, MODEL_CONSERVATIVE = 1 };
+
+// Scalar parameters of one step.
+template <typename T>
+struct StepArgs {
+    const T* __restrict__ fin; // f*(t-1), 9 planes
+    T* __restrict__ fout;      // f*(t), 9 planes
+    T* phi;                    // in: phi(t-1); out: phi(t)
+    double* mass_part;         // one FP64 partial per CTA
+    int nx, ny;
+    long long plane;           // nx * ny
+    int rows;                  // rows per CTA
+    int first;                 // t == 0: no time-derivative term
+    T omega;                   // 1 / tau
+    T fpref;                   // 1 - 1 / (2 tau)
+    T eps, inv_eps, inv4eps;   // eps, 1/eps, 1/(4 eps)
+    T delta, inv1p2d;          // regulariser d, 1/(1 + 2 d)
+};
+
+// Prescribed velocities. `col` caches what depends on x only; `at` gives u(t), u(t-1).
+template <typename T>
+struct VelVortex { // Eq. 14: u = A sx2[x] s2y[y] c(t), v = -A sy2[y] s2x[x] c(t)
+    const T* sx2; const T* s2x; const T* sy2; const T* s2y;
+    T amp, ct, ctm1;
+    struct Col { T sx2, s2x; };
+    __device__ __forceinline__ Col col(int x) const { return {sx2[x], s2x[x]}; }
+    __device__ __forceinline__ void at(const Col& c, int x, int y, T& u, T& v, T& up, T& vp) const
+    {
+        const T us = amp * c.sx2 * s2y[y];
+        const T vs = -amp * sy2[y] * c.s2x;
+        u = us * ct; v = vs * ct; up = us * ctm1; vp = vs * ctm1;
+    }
+};
+
+template <typename T>
+struct VelUniform {
+    T ux, uy;
+    struct Col {};
+    __device__ __forceinline__ Col col(int) const { return {}; }
+    __device__ __forceinline__ void at(const Col&, int, int, T& u, T& v, T& up, T& vp) const
+    {
+        u = ux; v = uy; up = ux; vp = uy;
+    }
+};
+
+template <typename T>
+struct VelPlanes { // device FP64 planes of u(t), v(t), u(t-1), v(t-1)
+    const double* u; const double* v; const double* up; const double* vp;
+    int nx;
+    struct Col {};
+    __device__ __forceinline__ Col col(int) const { return {}; }
+    __device__ __forceinline__ void at(const Col&, int x, int y, T& uu, T& vv, T& upp, T& vpp) const
+    {
+        const long long k = (long long)y * nx + x;
+        uu = T(u[k]); vv = T(v[k]); upp = T(up[k]); vpp = T(vp[k]);
+    }
+};
+
+// chi is the field whose isotropic gradient gives the normal: psi (Eq. 13) for the
+// paper's model, phi for the conservative-ACE ablation (Eq. 1).
+template <typename T, int MODEL>
+__device__ __forceinline__ T chi_of(T ph, const StepArgs<T>& a)
+{
+    if (MODEL == MODEL_MODIFIED) {
+        const T pc = ph < T(0) ? T(0) : (ph > T(1) ? T(1) : ph);
+        return a.eps * dlog((pc + a.delta) / (T(1) - pc + a.delta));
+    } else {
+        return ph;
+    }
+}
+
+// Population i of node (x, y) at time t, pulled from f*(t-1) at (x - c_i, y - c_i).
+// xm/xp/rm/rp are the wrapped neighbour column/row indices.
+template <typename T>
+__device__ __forceinline__ void pull_row(const T* __restrict__ fin, long long plane, int nx,
+                                         int r, int rm, int rp, int x, int xm, int xp, T* f)
+{
+    const T* p = fin;
+    f[0] = p[(long long)r * nx + x];   p += plane;
+    f[1] = p[(long long)r * nx + xm];  p += plane;
+    f[2] = p[(long long)rm * nx + x];  p += plane;
+    f[3] = p[(long long)r * nx + xp];  p += plane;
+    f[4] = p[(long long)rp * nx + x];  p += plane;
+    f[5] = p[(long long)rm * nx + xm]; p += plane;
+    f[6] = p[(long long)rm * nx + xp]; p += plane;
+    f[7] = p[(long long)rp * nx + xp]; p += plane;
+    f[8] = p[(long long)rp * nx + xm];
+}
+
+template <typename T, int MODEL, class Vel>
+__global__ void __launch_bounds__(TILE_X) ace_step(const StepArgs<T> a, const Vel vel)
+{
+    __shared__ T chi_s[4][TILE_X + 2];
+    __shared__ double red_s[TILE_X / 32];
+
+    const int tx = threadIdx.x;
+    const int lane = tx & 31;
+    const int x0 = blockIdx.x * TILE_X;
+    const int w = min(TILE_X, a.nx - x0);
+    const bool act = tx < w;
+    const int x = x0 + (act ? tx : 0);
+    const int xm = x == 0 ? a.nx - 1 : x - 1;
+    const int xp = x == a.nx - 1 ? 0 : x + 1;
+    const int y0 = blockIdx.y * a.rows;
+    const int y1 = min(y0 + a.rows, a.ny);
+    const int nk = y1 - y0 + 2; // rows y0-1 .. y1 get phi and chi
+
+    // Halo lanes of warp 0: lanes 0..8 pull population `hi` of the column left of
+    // the strip, lanes 16..24 that of the column right of it.
+    const bool halo = tx < 32 && (lane & 15) < 9;
+    const int hi = lane & 15;
+    int hcol = 0;
+    if (halo) {
+        const int c = lane < 16 ? (x0 == 0 ? a.nx - 1 : x0 - 1) : (x0 + w == a.nx ? 0 : x0 + w);
+        hcol = wrap_idx(c - cx_of(hi), a.nx);
+    }
+    const int hcy = halo ? cy_of(hi) : 0;
+    const T* hplane = a.fin + (long long)(halo ? hi : 0) * a.plane;
+
+    const typename Vel::Col vcol = vel.col(x);
+
+    T fa[9], fb[9];
+    T hv = T(0);
+    T phb = T(0);
+    double msum = 0.0;
+
+    {
+        const int r = wrap_idx(y0 - 1, a.ny);
+        if (act) pull_row(a.fin, a.plane, a.nx, r, wrap_idx(r - 1, a.ny), wrap_idx(r + 1, a.ny), x, xm, xp, fa);
+        if (halo) hv = hplane[(long long)wrap_idx(r - hcy, a.ny) * a.nx + hcol];
+    }
+
+    for (int k = 0; k < nk; ++k) {
+        // Row r = y0 - 1 + k: phi (Eq. 12) and chi into the ring slot k & 3.
+        T ph = T(0);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) ph += fa[i];
+        if (act) chi_s[k & 3][1 + tx] = chi_of<T, MODEL>(ph, a);
+        if (tx < 32) {
+            const int base = lane & 16;
+            T hs = T(0);
+#pragma unroll
+            for (int j = 0; j < 9; ++j) hs += __shfl_sync(0xffffffffu, hv, base + j);
+            if (lane == 0) chi_s[k & 3][0] = chi_of<T, MODEL>(hs, a);
+            if (lane == 16) chi_s[k & 3][w + 1] = chi_of<T, MODEL>(hs, a);
+        }
+        __syncthreads();
+
+        T fc[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) fc[i] = fa[i];
+        if (k + 1 < nk) { // prefetch row r + 1 while row r - 1 collides
+            const int r = wrap_idx(y0 + k, a.ny);
+            if (act) pull_row(a.fin, a.plane, a.nx, r, wrap_idx(r - 1, a.ny), wrap_idx(r + 1, a.ny), x, xm, xp, fa);
+            if (halo) hv = hplane[(long long)wrap_idx(r - hcy, a.ny) * a.nx + hcol];
+        }
+
+        if (k >= 2 && act) {
+            // Collide row yc = y0 + k - 2 with its pulled populations fb and phi phb.
+            const int yc = y0 + k - 2;
+            const T* cS = chi_s[(k - 2) & 3] + tx; // row yc - 1, index +1 = own column
+            const T* cC = chi_s[(k - 1) & 3] + tx; // row yc
+            const T* cN = chi_s[k & 3] + tx;       // row yc + 1
+            const T third = T(1) / T(3), twelfth = T(1) / T(12);
+            // 3 sum_i w_i c_i chi(x + c_i): axis neighbours 3/9, diagonals 3/36
+            const T gx = (cC[2] - cC[0]) * third + ((cN[2] - cN[0]) + (cS[2] - cS[0])) * twelfth;
+            const T gy = (cN[1] - cS[1]) * third + ((cN[2] + cN[0]) - (cS[2] + cS[0])) * twelfth;
+            const T inv = T(1) / (dsqrt(gx * gx + gy * gy) + a.delta);
+            const T nxv = gx * inv, nyv = gy * inv;
+            T S;
+            if (MODEL == MODEL_MODIFIED) {
+                const T pc = phb < T(0) ? T(0) : (phb > T(1) ? T(1) : phb);
+                const T th = (T(2) * pc - T(1)) * a.inv1p2d;
+                S = (T(1) - th * th) * a.inv4eps;
+            } else {
+                S = phb * (T(1) - phb) * a.inv_eps;
+            }
+            T u, v, up, vp;
+            vel.at(vcol, x, yc, u, v, up, vp);
+            T* phr = a.phi + (long long)yc * a.nx + x;
+            T dx = T(0), dy = T(0);
+            if (!a.first) {
+                const T pp = *phr;
+                dx = phb * u - pp * up;
+                dy = phb * v - pp * vp;
+            }
+            const T Gx = dx + S * nxv * third; // bracket of Eq. 11: d_t(phi u) + c_s^2 S n
+            const T Gy = dy + S * nyv * third;
+            const T om1 = T(1) - a.omega;
+            T* o = a.fout + (long long)yc * a.nx + x;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                const T cu = T(cx_of(i)) * u + T(cy_of(i)) * v;
+                const T cg = T(cx_of(i)) * Gx + T(cy_of(i)) * Gy;
+                const T feq = w_of<T>(i) * phb * (T(1) + T(3) * cu);
+                const T F = T(3) * w_of<T>(i) * cg;
+                o[(long long)i * a.plane] = fb[i] * om1 + a.omega * feq + a.fpref * F;
+            }
+            *phr = phb;
+            msum += (double)phb;
+        }
+#pragma unroll
+        for (int i = 0; i < 9; ++i) fb[i] = fc[i];
+        phb = ph;
+    }
+
+    // a13: block-reduced mass of phi(t) over the CTA's nodes, fixed order.
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) msum += __shfl_down_sync(0xffffffffu, msum, off);
+    if (lane == 0) red_s[tx >> 5] = msum;
+    __syncthreads();
+    if (tx == 0) {
+        double s = 0.0;
+#pragma unroll
+        for (int i = 0; i < TILE_X / 32; ++i) s += red_s[i];
+        a.mass_part[(long long)blockIdx.y * gridDim.x + blockIdx.x] = s;
+    }
+}
+
+// Initial state (R7): f_i(x, 0) = f_i^eq(phi0(x), u(x, 0)). Stored as the post-
+// collision buffer f*(-1) from which the first step pulls: f*_i(x) = f_i(x + c_i, 0).
+template <typename T, class Vel>
+__global__ void ace_init(const double* __restrict__ phi0, T* __restrict__ fst, T* __restrict__ phi,
+                         int nx, int ny, Vel vel)
+{
+    const long long plane = (long long)nx * ny;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < plane;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(k % nx), y = (int)(k / nx);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const int sx = wrap_idx(x + cx_of(i), nx), sy = wrap_idx(y + cy_of(i), ny);
+            const T ph = T(phi0[(long long)sy * nx + sx]);
+            T u, v, up, vp;
+            vel.at(vel.col(sx), sx, sy, u, v, up, vp);
+            const T cu = T(cx_of(i)) * u + T(cy_of(i)) * v;
+            fst[i * plane + k] = w_of<T>(i) * ph * (T(1) + T(3) * cu);
+        }
+        phi[k] = T(phi0[k]);
+    }
+}
+
+// phi(x, t) = sum_i f*_i(x - c_i, t - 1) (Eq. 12 after streaming), as FP64.
+template <typename T>
+__global__ void ace_moment(const T* __restrict__ fst, double* __restrict__ out, int nx, int ny)
+{
+    const long long plane = (long long)nx * ny;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < plane;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(k % nx), y = (int)(k / nx);
+        T s = T(0);
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+            s += fst[i * plane + (long long)wrap_idx(y - cy_of(i), ny) * nx + wrap_idx(x - cx_of(i), nx)];
+        out[k] = (double)s;
+    }
+}
+
+// Checkpoint read: f_i(x, t) = f*_i(x - c_i, t - 1) as FP64, and phi(t-1).
+template <typename T>
+__global__ void ace_pull_state(const T* __restrict__ fst, const T* __restrict__ phi,
+                               double* __restrict__ f, double* __restrict__ php, int nx, int ny)
+{
+    const long long plane = (long long)nx * ny;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < plane;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(k % nx), y = (int)(k / nx);
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+            f[i * plane + k] =
+                (double)fst[i * plane + (long long)wrap_idx(y - cy_of(i), ny) * nx + wrap_idx(x - cx_of(i), nx)];
+        php[k] = (double)phi[k];
+    }
+}
+
+// Checkpoint write: f*_i(x) = f_i(x + c_i) rounded to T, phi plane = phi(t-1).
+template <typename T>
+__global__ void ace_push_state(const double* __restrict__ f, const double* __restrict__ php,
+                               T* __restrict__ fst, T* __restrict__ phi, int nx, int ny)
+{
+    const long long plane = (long long)nx * ny;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < plane;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(k % nx), y = (int)(k / nx);
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+            fst[i * plane + k] =
+                T(f[i * plane + (long long)wrap_idx(y + cy_of(i), ny) * nx + wrap_idx(x + cx_of(i), nx)]);
+        phi[k] = T(php[k]);
+    }
+}
+
+// Neumaier-compensated accumulation.
+__device__ __forceinline__ void neumaier(double& s, double& c, double v)
+{
+    const double t = s + v;
+    c += fabs(s) >= fabs(v) ? (s - t) + v : (v - t) + s;
+    s = t;
+}
+
+constexpr int RED_THREADS = 256;
+
+// Partial sums of n values of T: each thread sums a fixed strided subset with
+// compensation, the CTA combines in a fixed tree order. Deterministic.
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS) ace_sum_partials(const T* __restrict__ v, long long n,
+                                                                double* __restrict__ part)
+{
+    __shared__ double sh[RED_THREADS];
+    double s = 0.0, c = 0.0;
+    for (long long k = blockIdx.x * (long long)RED_THREADS + threadIdx.x; k < n;
+         k += (long long)gridDim.x * RED_THREADS)
+        neumaier(s, c, (double)v[k]);
+    sh[threadIdx.x] = s + c;
+    __syncthreads();
+    for (int h = RED_THREADS / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) sh[threadIdx.x] += sh[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+// Final sum of n partials by one warp: per-lane compensated sums over a strided
+// subset, then lane 0 combines the 32 (sum, compensation) pairs in lane order.
+__global__ void ace_finalize(const double* __restrict__ part, int n, double* __restrict__ out)
+{
+    const int lane = threadIdx.x;
+    double s = 0.0, c = 0.0;
+    for (int k = lane; k < n; k += 32) neumaier(s, c, part[k]);
+    double S = 0.0, C = 0.0;
+    for (int j = 0; j < 32; ++j) {
+        const double sj = __shfl_sync(0xffffffffu, s, j);
+        const double cj = __shfl_sync(0xffffffffu, c, j);
+        neumaier(S, C, sj);
+        neumaier(S, C, cj);
+    }
+    if (lane == 0) out[0] = S + C;
+}
+
+} // namespace lbmace

@@ -1,0 +1,611 @@
+// lbm_ace.cu -- host side of the C ABI declared in include/lbm_ace.h.
+//
+// Owns the device state of one lattice (two ping-pong population buffers, the phi
+// plane, velocity tables or planes, reduction partials), validates parameters,
+// and issues one fused step kernel per time step on the caller's stream.
+#include "lbm_ace.h"
+#include "ace_kernels.cuh"
+
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+using namespace lbmace;
+
+namespace {
+
+thread_local std::string g_err; // errors raised before a context exists
+
+constexpr double kPi = 3.14159265358979323846;
+
+struct VelState {
+    // single vortex tables, in the storage precision of the arithmetic (T)
+    void* sx2 = nullptr; void* s2x = nullptr; void* sy2 = nullptr; void* s2y = nullptr;
+    // FP64 planes for field / callback velocities: pair 0 and pair 1
+    double* pu[2] = {nullptr, nullptr};
+    double* pv[2] = {nullptr, nullptr};
+    int cur = 0; // pair holding u(t)
+    std::vector<double> hu, hv; // host buffers for the callback
+};
+
+} // namespace
+
+struct lbm_ace_ctx {
+    lbm_ace_params p{};
+    cudaStream_t stream = nullptr;
+    int dev = 0;
+    int sms = 0;
+    size_t elem = 0;        // bytes per stored value
+    void* f[2] = {nullptr, nullptr};
+    int cur = 0;            // buffer holding f*(t-1)
+    void* phi = nullptr;    // phi(t-1) plane
+    double* step_part = nullptr; int n_step_part = 0;
+    double* red_part = nullptr; int n_red_part = 0;
+    double* result = nullptr;
+    double* scratch = nullptr; size_t scratch_elems = 0; // FP64 staging for state/phi copies
+    VelState vel;
+    long long t = 0;
+    bool stepped = false;
+    int rows = 0, grid_x = 0, grid_y = 0;
+    std::string err;
+};
+
+namespace {
+
+int fail(lbm_ace_ctx* c, int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf; else g_err = buf;
+    return code;
+}
+
+#define CK(ctx, call)                                                                         \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail((ctx), e_ == cudaErrorMemoryAllocation ? LBM_ACE_ENOMEM : LBM_ACE_ECUDA, \
+                        "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__);  \
+    } while (0)
+
+int grid_for(long long n, int sms) // grid of a grid-stride elementwise kernel
+{
+    long long g = (n + 255) / 256;
+    long long cap = (long long)sms * 8;
+    if (g > cap) g = cap;
+    return (int)(g < 1 ? 1 : g);
+}
+
+// --- typed dispatch -----------------------------------------------------------
+
+template <typename T>
+StepArgs<T> make_args(lbm_ace_ctx* c)
+{
+    StepArgs<T> a;
+    a.fin = (const T*)c->f[c->cur];
+    a.fout = (T*)c->f[1 - c->cur];
+    a.phi = (T*)c->phi;
+    a.mass_part = c->step_part;
+    a.nx = c->p.nx; a.ny = c->p.ny;
+    a.plane = (long long)c->p.nx * c->p.ny;
+    a.rows = c->rows;
+    a.first = c->t == 0;
+    a.omega = T(1.0 / c->p.tau);
+    a.fpref = T(1.0 - 0.5 / c->p.tau);
+    a.eps = T(c->p.eps);
+    a.inv_eps = T(1.0 / c->p.eps);
+    a.inv4eps = T(0.25 / c->p.eps);
+    a.delta = T(c->p.reg_delta);
+    a.inv1p2d = T(1.0 / (1.0 + 2.0 * c->p.reg_delta));
+    return a;
+}
+
+template <typename T>
+VelVortex<T> vortex(lbm_ace_ctx* c, double t)
+{
+    VelVortex<T> v;
+    v.sx2 = (const T*)c->vel.sx2; v.s2x = (const T*)c->vel.s2x;
+    v.sy2 = (const T*)c->vel.sy2; v.s2y = (const T*)c->vel.s2y;
+    v.amp = T(c->p.vortex_sign * c->p.U0);
+    v.ct = T(std::cos(kPi * t / c->p.T_period));
+    v.ctm1 = T(std::cos(kPi * (t - 1.0) / c->p.T_period));
+    return v;
+}
+
+template <typename T>
+VelPlanes<T> planes(lbm_ace_ctx* c)
+{
+    VelPlanes<T> v;
+    const int cu = c->vel.cur;
+    // FIELD: one static pair; CALLBACK: u(t) in pair `cur`, u(t-1) in the other
+    const int pv = c->p.velocity_kind == LBM_ACE_VEL_CALLBACK && c->t > 0 ? 1 - cu : cu;
+    v.u = c->vel.pu[cu]; v.v = c->vel.pv[cu];
+    v.up = c->vel.pu[pv]; v.vp = c->vel.pv[pv];
+    v.nx = c->p.nx;
+    return v;
+}
+
+template <typename T, int MODEL, class Vel>
+void launch_step_k(lbm_ace_ctx* c, const Vel& vel)
+{
+    dim3 grid(c->grid_x, c->grid_y);
+    ace_step<T, MODEL, Vel><<<grid, TILE_X, 0, c->stream>>>(make_args<T>(c), vel);
+}
+
+template <typename T, int MODEL>
+void launch_step_m(lbm_ace_ctx* c)
+{
+    switch (c->p.velocity_kind) {
+    case LBM_ACE_VEL_SINGLE_VORTEX: launch_step_k<T, MODEL>(c, vortex<T>(c, (double)c->t)); break;
+    case LBM_ACE_VEL_UNIFORM: {
+        VelUniform<T> v; v.ux = T(c->p.ux); v.uy = T(c->p.uy);
+        launch_step_k<T, MODEL>(c, v);
+        break;
+    }
+    default: launch_step_k<T, MODEL>(c, planes<T>(c)); break;
+    }
+}
+
+template <typename T>
+void launch_step_t(lbm_ace_ctx* c)
+{
+    if (c->p.model == LBM_ACE_MODEL_MODIFIED) launch_step_m<T, MODEL_MODIFIED>(c);
+    else launch_step_m<T, MODEL_CONSERVATIVE>(c);
+}
+
+template <typename T>
+void launch_init_t(lbm_ace_ctx* c, const double* dphi0)
+{
+    const long long n = (long long)c->p.nx * c->p.ny;
+    const int g = grid_for(n, c->sms);
+    T* fst = (T*)c->f[c->cur];
+    T* phi = (T*)c->phi;
+    switch (c->p.velocity_kind) {
+    case LBM_ACE_VEL_SINGLE_VORTEX:
+        ace_init<T><<<g, 256, 0, c->stream>>>(dphi0, fst, phi, c->p.nx, c->p.ny, vortex<T>(c, 0.0));
+        break;
+    case LBM_ACE_VEL_UNIFORM: {
+        VelUniform<T> v; v.ux = T(c->p.ux); v.uy = T(c->p.uy);
+        ace_init<T><<<g, 256, 0, c->stream>>>(dphi0, fst, phi, c->p.nx, c->p.ny, v);
+        break;
+    }
+    default:
+        ace_init<T><<<g, 256, 0, c->stream>>>(dphi0, fst, phi, c->p.nx, c->p.ny, planes<T>(c));
+        break;
+    }
+}
+
+template <typename T>
+int fill_vortex_tables(lbm_ace_ctx* c)
+{
+    const int nx = c->p.nx, ny = c->p.ny;
+    std::vector<T> sx2(nx), s2x(nx), sy2(ny), s2y(ny);
+    for (int x = 0; x < nx; ++x) {
+        const double s = std::sin(kPi * x / nx);
+        sx2[x] = T(s * s);
+        s2x[x] = T(std::sin(2.0 * kPi * x / nx));
+    }
+    for (int y = 0; y < ny; ++y) {
+        const double s = std::sin(kPi * y / ny);
+        sy2[y] = T(s * s);
+        s2y[y] = T(std::sin(2.0 * kPi * y / ny));
+    }
+    CK(c, cudaMalloc(&c->vel.sx2, nx * sizeof(T)));
+    CK(c, cudaMalloc(&c->vel.s2x, nx * sizeof(T)));
+    CK(c, cudaMalloc(&c->vel.sy2, ny * sizeof(T)));
+    CK(c, cudaMalloc(&c->vel.s2y, ny * sizeof(T)));
+    CK(c, cudaMemcpy(c->vel.sx2, sx2.data(), nx * sizeof(T), cudaMemcpyHostToDevice));
+    CK(c, cudaMemcpy(c->vel.s2x, s2x.data(), nx * sizeof(T), cudaMemcpyHostToDevice));
+    CK(c, cudaMemcpy(c->vel.sy2, sy2.data(), ny * sizeof(T), cudaMemcpyHostToDevice));
+    CK(c, cudaMemcpy(c->vel.s2y, s2y.data(), ny * sizeof(T), cudaMemcpyHostToDevice));
+    return LBM_ACE_OK;
+}
+
+template <typename T>
+int occupancy_t(lbm_ace_ctx* c, int* blocks)
+{
+    cudaError_t e;
+    const bool mod = c->p.model == LBM_ACE_MODEL_MODIFIED;
+    switch (c->p.velocity_kind) {
+    case LBM_ACE_VEL_SINGLE_VORTEX:
+        e = mod ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, ace_step<T, MODEL_MODIFIED, VelVortex<T>>, TILE_X, 0)
+                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, ace_step<T, MODEL_CONSERVATIVE, VelVortex<T>>, TILE_X, 0);
+        break;
+    case LBM_ACE_VEL_UNIFORM:
+        e = mod ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, ace_step<T, MODEL_MODIFIED, VelUniform<T>>, TILE_X, 0)
+                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, ace_step<T, MODEL_CONSERVATIVE, VelUniform<T>>, TILE_X, 0);
+        break;
+    default:
+        e = mod ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, ace_step<T, MODEL_MODIFIED, VelPlanes<T>>, TILE_X, 0)
+                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, ace_step<T, MODEL_CONSERVATIVE, VelPlanes<T>>, TILE_X, 0);
+        break;
+    }
+    CK(c, e);
+    return LBM_ACE_OK;
+}
+
+bool is_f64(const lbm_ace_ctx* c) { return c->p.precision == LBM_ACE_F64; }
+
+int ensure_scratch(lbm_ace_ctx* c, size_t elems)
+{
+    if (c->scratch_elems >= elems) return LBM_ACE_OK;
+    if (c->scratch) cudaFree(c->scratch);
+    c->scratch = nullptr;
+    c->scratch_elems = 0;
+    CK(c, cudaMalloc(&c->scratch, elems * sizeof(double)));
+    c->scratch_elems = elems;
+    return LBM_ACE_OK;
+}
+
+// Velocity planes for time t from the host callback into pair `pair`.
+int callback_upload(lbm_ace_ctx* c, double t, int pair)
+{
+    const size_t n = (size_t)c->p.nx * c->p.ny;
+    const int rc = c->p.vel_fn(t, c->p.nx, c->p.ny, c->vel.hu.data(), c->vel.hv.data(), c->p.vel_user);
+    if (rc != 0) return fail(c, LBM_ACE_ECALLBACK, "velocity callback returned %d at t = %g", rc, t);
+    CK(c, cudaMemcpyAsync(c->vel.pu[pair], c->vel.hu.data(), n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CK(c, cudaMemcpyAsync(c->vel.pv[pair], c->vel.hv.data(), n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    // the pageable source is staged before return, but keep the host buffer stable
+    CK(c, cudaStreamSynchronize(c->stream));
+    return LBM_ACE_OK;
+}
+
+int finalize_sum(lbm_ace_ctx* c, const double* part, int n, double* out)
+{
+    ace_finalize<<<1, 32, 0, c->stream>>>(part, n, c->result);
+    CK(c, cudaGetLastError());
+    CK(c, cudaMemcpyAsync(out, c->result, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return LBM_ACE_OK;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int d) { if (cudaGetDevice(&prev) == cudaSuccess && prev != d) cudaSetDevice(d); else prev = -1; }
+    ~DeviceGuard() { if (prev >= 0) cudaSetDevice(prev); }
+};
+
+} // namespace
+
+extern "C" {
+
+int lbm_ace_params_default(lbm_ace_params* p)
+{
+    if (!p) return fail(nullptr, LBM_ACE_EINVAL, "params is NULL");
+    std::memset(p, 0, sizeof *p);
+    p->nx = p->ny = 64;
+    p->tau = 0.8;
+    p->M = -1.0;
+    p->eps = 1.0;
+    p->reg_delta = 0.0;
+    p->precision = LBM_ACE_F64;
+    p->model = LBM_ACE_MODEL_MODIFIED;
+    p->velocity_kind = LBM_ACE_VEL_SINGLE_VORTEX;
+    p->U0 = 0.04;
+    p->T_period = 2000.0;
+    p->vortex_sign = -1.0;
+    p->xc = 32.0; p->yc = 48.0; p->R = 9.6;
+    return LBM_ACE_OK;
+}
+
+const char* lbm_ace_status_string(int s)
+{
+    switch (s) {
+    case LBM_ACE_OK: return "ok";
+    case LBM_ACE_EINVAL: return "invalid argument";
+    case LBM_ACE_ENOMEM: return "out of memory";
+    case LBM_ACE_ECUDA: return "CUDA error";
+    case LBM_ACE_ENUMERIC: return "non-finite values";
+    case LBM_ACE_ETIMEOUT: return "device wait timed out";
+    case LBM_ACE_ECALLBACK: return "velocity callback failed";
+    default: return "unknown status";
+    }
+}
+
+const char* lbm_ace_last_error(const lbm_ace_ctx* c) { return c ? c->err.c_str() : g_err.c_str(); }
+
+long long lbm_ace_steps_done(const lbm_ace_ctx* c) { return c ? c->t : -1; }
+
+void lbm_ace_destroy(lbm_ace_ctx* c)
+{
+    if (!c) return;
+    DeviceGuard g(c->dev);
+    if (c->stream) cudaStreamSynchronize(c->stream); else cudaDeviceSynchronize();
+    void* bufs[] = {c->f[0], c->f[1], c->phi, c->step_part, c->red_part, c->result, c->scratch,
+                    c->vel.sx2, c->vel.s2x, c->vel.sy2, c->vel.s2y,
+                    c->vel.pu[0], c->vel.pu[1], c->vel.pv[0], c->vel.pv[1]};
+    for (void* b : bufs) if (b) cudaFree(b);
+    delete c;
+}
+
+static int init_impl(lbm_ace_ctx* c, const lbm_ace_params* p)
+{
+    c->p = *p;
+    if (c->p.reg_delta == 0.0) c->p.reg_delta = std::exp(-20.0);
+    c->dev = p->device;
+    c->stream = (cudaStream_t)p->stream;
+    CK(c, cudaSetDevice(c->dev));
+    CK(c, cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->dev));
+    const int nx = p->nx, ny = p->ny;
+    const size_t n = (size_t)nx * ny;
+    c->elem = is_f64(c) ? sizeof(double) : sizeof(float);
+
+    CK(c, cudaMalloc(&c->f[0], 9 * n * c->elem));
+    CK(c, cudaMalloc(&c->f[1], 9 * n * c->elem));
+    CK(c, cudaMalloc(&c->phi, n * c->elem));
+    CK(c, cudaMalloc(&c->result, 2 * sizeof(double)));
+
+    // launch shape of the fused step: one wave of resident CTAs when possible
+    int occ = 0;
+    int rc = is_f64(c) ? occupancy_t<double>(c, &occ) : occupancy_t<float>(c, &occ);
+    if (rc) return rc;
+    if (occ < 1) occ = 1;
+    c->grid_x = (nx + TILE_X - 1) / TILE_X;
+    int rows = p->rows_per_cta;
+    if (rows <= 0) {
+        const long long slots = (long long)c->sms * occ;
+        long long r = ((long long)ny * c->grid_x + slots - 1) / slots;
+        if (r < 4) r = 4;
+        if (r > 64) r = 64;
+        rows = (int)r;
+    }
+    if (rows > ny) rows = ny;
+    c->rows = rows;
+    c->grid_y = (ny + rows - 1) / rows;
+    c->n_step_part = c->grid_x * c->grid_y;
+    CK(c, cudaMalloc(&c->step_part, c->n_step_part * sizeof(double)));
+    c->n_red_part = grid_for(9 * (long long)n, c->sms);
+    CK(c, cudaMalloc(&c->red_part, c->n_red_part * sizeof(double)));
+
+    // velocity
+    if (p->velocity_kind == LBM_ACE_VEL_SINGLE_VORTEX) {
+        rc = is_f64(c) ? fill_vortex_tables<double>(c) : fill_vortex_tables<float>(c);
+        if (rc) return rc;
+    } else if (p->velocity_kind == LBM_ACE_VEL_FIELD || p->velocity_kind == LBM_ACE_VEL_CALLBACK) {
+        const int pairs = p->velocity_kind == LBM_ACE_VEL_CALLBACK ? 2 : 1;
+        for (int k = 0; k < pairs; ++k) {
+            CK(c, cudaMalloc(&c->vel.pu[k], n * sizeof(double)));
+            CK(c, cudaMalloc(&c->vel.pv[k], n * sizeof(double)));
+        }
+        if (pairs == 1) {
+            CK(c, cudaMemcpy(c->vel.pu[0], p->u_field, n * sizeof(double), cudaMemcpyHostToDevice));
+            CK(c, cudaMemcpy(c->vel.pv[0], p->v_field, n * sizeof(double), cudaMemcpyHostToDevice));
+        } else {
+            c->vel.hu.assign(n, 0.0);
+            c->vel.hv.assign(n, 0.0);
+            c->vel.cur = 0;
+            rc = callback_upload(c, 0.0, 0);
+            if (rc) return rc;
+        }
+    }
+
+    // initial phi: host array or the disk
+    rc = ensure_scratch(c, n);
+    if (rc) return rc;
+    if (p->phi0) {
+        CK(c, cudaMemcpyAsync(c->scratch, p->phi0, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    } else {
+        std::vector<double> h(n);
+        for (int y = 0; y < ny; ++y)
+            for (int x = 0; x < nx; ++x) {
+                const double r = std::sqrt((x - p->xc) * (x - p->xc) + (y - p->yc) * (y - p->yc));
+                h[(size_t)y * nx + x] = 0.5 * (1.0 + std::tanh((p->R - r) / (2.0 * p->eps)));
+            }
+        CK(c, cudaMemcpyAsync(c->scratch, h.data(), n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        CK(c, cudaStreamSynchronize(c->stream));
+    }
+    c->cur = 0;
+    c->t = 0;
+    if (is_f64(c)) launch_init_t<double>(c, c->scratch); else launch_init_t<float>(c, c->scratch);
+    CK(c, cudaGetLastError());
+    CK(c, cudaStreamSynchronize(c->stream));
+    return LBM_ACE_OK;
+}
+
+int lbm_ace_init(const lbm_ace_params* p, lbm_ace_ctx** out)
+{
+    if (!out) return fail(nullptr, LBM_ACE_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!p) return fail(nullptr, LBM_ACE_EINVAL, "params is NULL");
+    if (p->nx < 3 || p->ny < 3) return fail(nullptr, LBM_ACE_EINVAL, "lattice %d x %d: each side must be >= 3", p->nx, p->ny);
+    if ((long long)p->nx * p->ny > (1LL << 31) / 9) return fail(nullptr, LBM_ACE_EINVAL, "lattice %d x %d too large", p->nx, p->ny);
+    if (!(p->tau > 0.5) || !std::isfinite(p->tau)) return fail(nullptr, LBM_ACE_EINVAL, "tau = %g: must be > 0.5", p->tau);
+    if (!(p->eps > 0.0) || !std::isfinite(p->eps)) return fail(nullptr, LBM_ACE_EINVAL, "eps = %g: must be > 0", p->eps);
+    if (p->reg_delta < 0.0 || !std::isfinite(p->reg_delta)) return fail(nullptr, LBM_ACE_EINVAL, "reg_delta = %g: must be >= 0", p->reg_delta);
+    if (p->M >= 0.0) {
+        const double m = (p->tau - 0.5) / 3.0;
+        if (std::fabs(p->M - m) > 1e-12 * m)
+            return fail(nullptr, LBM_ACE_EINVAL, "M = %.17g differs from c_s^2 (tau - 0.5) = %.17g", p->M, m);
+    }
+    if (p->precision != LBM_ACE_F64 && p->precision != LBM_ACE_F32)
+        return fail(nullptr, LBM_ACE_EINVAL, "precision %d is not available in this build", p->precision);
+    if (p->model != LBM_ACE_MODEL_MODIFIED && p->model != LBM_ACE_MODEL_CONSERVATIVE)
+        return fail(nullptr, LBM_ACE_EINVAL, "model %d unknown", p->model);
+    switch (p->velocity_kind) {
+    case LBM_ACE_VEL_SINGLE_VORTEX:
+        if (!(p->T_period > 0.0) || !std::isfinite(p->U0) || !std::isfinite(p->vortex_sign))
+            return fail(nullptr, LBM_ACE_EINVAL, "single vortex needs T_period > 0 and finite U0, vortex_sign");
+        break;
+    case LBM_ACE_VEL_UNIFORM:
+        if (!std::isfinite(p->ux) || !std::isfinite(p->uy)) return fail(nullptr, LBM_ACE_EINVAL, "uniform velocity not finite");
+        break;
+    case LBM_ACE_VEL_FIELD:
+        if (!p->u_field || !p->v_field) return fail(nullptr, LBM_ACE_EINVAL, "velocity field arrays are NULL");
+        break;
+    case LBM_ACE_VEL_CALLBACK:
+        if (!p->vel_fn) return fail(nullptr, LBM_ACE_EINVAL, "velocity callback is NULL");
+        break;
+    default: return fail(nullptr, LBM_ACE_EINVAL, "velocity kind %d unknown", p->velocity_kind);
+    }
+    if (p->phi0) {
+        const size_t n = (size_t)p->nx * p->ny;
+        for (size_t k = 0; k < n; ++k)
+            if (!std::isfinite(p->phi0[k]))
+                return fail(nullptr, LBM_ACE_EINVAL, "phi0[%zu] is not finite", k);
+    } else if (!std::isfinite(p->xc) || !std::isfinite(p->yc) || !std::isfinite(p->R)) {
+        return fail(nullptr, LBM_ACE_EINVAL, "disk centre/radius not finite");
+    }
+    if (p->rows_per_cta < 0) return fail(nullptr, LBM_ACE_EINVAL, "rows_per_cta must be >= 0");
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || p->device < 0 || p->device >= ndev)
+        return fail(nullptr, LBM_ACE_ECUDA, "CUDA device %d unavailable (%s)", p->device,
+                    e == cudaSuccess ? "ordinal out of range" : cudaGetErrorString(e));
+
+    lbm_ace_ctx* c = new (std::nothrow) lbm_ace_ctx;
+    if (!c) return fail(nullptr, LBM_ACE_ENOMEM, "host allocation failed");
+    DeviceGuard g(p->device);
+    const int rc = init_impl(c, p);
+    if (rc != LBM_ACE_OK) {
+        g_err = c->err;
+        lbm_ace_destroy(c);
+        return rc;
+    }
+    *out = c;
+    return LBM_ACE_OK;
+}
+
+int lbm_ace_step(lbm_ace_ctx* c, long long n)
+{
+    if (!c) return fail(nullptr, LBM_ACE_EINVAL, "ctx is NULL");
+    if (n < 0) return fail(c, LBM_ACE_EINVAL, "n = %lld: must be >= 0", n);
+    DeviceGuard g(c->dev);
+    for (long long s = 0; s < n; ++s) {
+        if (c->p.velocity_kind == LBM_ACE_VEL_CALLBACK && c->t > 0) {
+            // u(t) into the pair that held u(t-2); the pair with u(t-1) becomes "previous"
+            const int next = 1 - c->vel.cur;
+            const int rc = callback_upload(c, (double)c->t, next);
+            if (rc) return rc;
+            c->vel.cur = next;
+        }
+        if (is_f64(c)) launch_step_t<double>(c); else launch_step_t<float>(c);
+        CK(c, cudaGetLastError());
+        c->cur = 1 - c->cur;
+        c->t += 1;
+        c->stepped = true;
+    }
+    return LBM_ACE_OK;
+}
+
+int lbm_ace_get_phi(lbm_ace_ctx* c, double* out, size_t count)
+{
+    if (!c) return fail(nullptr, LBM_ACE_EINVAL, "ctx is NULL");
+    const size_t n = (size_t)c->p.nx * c->p.ny;
+    if (!out || count != n) return fail(c, LBM_ACE_EINVAL, "out must hold nx*ny = %zu values (got %zu)", n, count);
+    DeviceGuard g(c->dev);
+    int rc = ensure_scratch(c, n);
+    if (rc) return rc;
+    const int gr = grid_for((long long)n, c->sms);
+    if (is_f64(c)) ace_moment<double><<<gr, 256, 0, c->stream>>>((const double*)c->f[c->cur], c->scratch, c->p.nx, c->p.ny);
+    else ace_moment<float><<<gr, 256, 0, c->stream>>>((const float*)c->f[c->cur], c->scratch, c->p.nx, c->p.ny);
+    CK(c, cudaGetLastError());
+    CK(c, cudaMemcpyAsync(out, c->scratch, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return LBM_ACE_OK;
+}
+
+int lbm_ace_mass(lbm_ace_ctx* c, double* out)
+{
+    if (!c) return fail(nullptr, LBM_ACE_EINVAL, "ctx is NULL");
+    if (!out) return fail(c, LBM_ACE_EINVAL, "out is NULL");
+    DeviceGuard g(c->dev);
+    const long long n9 = 9LL * c->p.nx * c->p.ny;
+    if (is_f64(c)) ace_sum_partials<double><<<c->n_red_part, RED_THREADS, 0, c->stream>>>((const double*)c->f[c->cur], n9, c->red_part);
+    else ace_sum_partials<float><<<c->n_red_part, RED_THREADS, 0, c->stream>>>((const float*)c->f[c->cur], n9, c->red_part);
+    CK(c, cudaGetLastError());
+    const int rc = finalize_sum(c, c->red_part, c->n_red_part, out);
+    if (rc) return rc;
+    if (!std::isfinite(*out)) return fail(c, LBM_ACE_ENUMERIC, "global mass is not finite (%g)", *out);
+    return LBM_ACE_OK;
+}
+
+int lbm_ace_step_mass(lbm_ace_ctx* c, double* out)
+{
+    if (!c) return fail(nullptr, LBM_ACE_EINVAL, "ctx is NULL");
+    if (!out) return fail(c, LBM_ACE_EINVAL, "out is NULL");
+    if (!c->stepped) return fail(c, LBM_ACE_EINVAL, "no step has run yet");
+    DeviceGuard g(c->dev);
+    const int rc = finalize_sum(c, c->step_part, c->n_step_part, out);
+    if (rc) return rc;
+    if (!std::isfinite(*out)) return fail(c, LBM_ACE_ENUMERIC, "step mass is not finite (%g)", *out);
+    return LBM_ACE_OK;
+}
+
+int lbm_ace_get_state(lbm_ace_ctx* c, double* f, double* phi_prev)
+{
+    if (!c) return fail(nullptr, LBM_ACE_EINVAL, "ctx is NULL");
+    DeviceGuard g(c->dev);
+    const size_t n = (size_t)c->p.nx * c->p.ny;
+    int rc = ensure_scratch(c, 10 * n);
+    if (rc) return rc;
+    const int gr = grid_for((long long)n, c->sms);
+    if (is_f64(c))
+        ace_pull_state<double><<<gr, 256, 0, c->stream>>>((const double*)c->f[c->cur], (const double*)c->phi,
+                                                          c->scratch, c->scratch + 9 * n, c->p.nx, c->p.ny);
+    else
+        ace_pull_state<float><<<gr, 256, 0, c->stream>>>((const float*)c->f[c->cur], (const float*)c->phi,
+                                                         c->scratch, c->scratch + 9 * n, c->p.nx, c->p.ny);
+    CK(c, cudaGetLastError());
+    if (f) CK(c, cudaMemcpyAsync(f, c->scratch, 9 * n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if (phi_prev) CK(c, cudaMemcpyAsync(phi_prev, c->scratch + 9 * n, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return LBM_ACE_OK;
+}
+
+int lbm_ace_set_state(lbm_ace_ctx* c, const double* f, const double* phi_prev, long long t)
+{
+    if (!c) return fail(nullptr, LBM_ACE_EINVAL, "ctx is NULL");
+    if (!f || !phi_prev) return fail(c, LBM_ACE_EINVAL, "f and phi_prev are required");
+    if (t < 0) return fail(c, LBM_ACE_EINVAL, "t = %lld: must be >= 0", t);
+    if (c->p.velocity_kind == LBM_ACE_VEL_CALLBACK)
+        return fail(c, LBM_ACE_EINVAL, "set_state is not supported with a velocity callback");
+    DeviceGuard g(c->dev);
+    const size_t n = (size_t)c->p.nx * c->p.ny;
+    for (size_t k = 0; k < 9 * n; ++k)
+        if (!std::isfinite(f[k])) return fail(c, LBM_ACE_EINVAL, "f[%zu] is not finite", k);
+    int rc = ensure_scratch(c, 10 * n);
+    if (rc) return rc;
+    CK(c, cudaMemcpyAsync(c->scratch, f, 9 * n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CK(c, cudaMemcpyAsync(c->scratch + 9 * n, phi_prev, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    const int gr = grid_for((long long)n, c->sms);
+    if (is_f64(c))
+        ace_push_state<double><<<gr, 256, 0, c->stream>>>(c->scratch, c->scratch + 9 * n, (double*)c->f[c->cur],
+                                                          (double*)c->phi, c->p.nx, c->p.ny);
+    else
+        ace_push_state<float><<<gr, 256, 0, c->stream>>>(c->scratch, c->scratch + 9 * n, (float*)c->f[c->cur],
+                                                         (float*)c->phi, c->p.nx, c->p.ny);
+    CK(c, cudaGetLastError());
+    CK(c, cudaStreamSynchronize(c->stream));
+    c->t = t;
+    c->stepped = false;
+    return LBM_ACE_OK;
+}
+
+int lbm_ace_launch_shape(const lbm_ace_ctx* c, int* tile_x, int* rows_per_cta, int* grid_x, int* grid_y)
+{
+    if (!c) return fail(nullptr, LBM_ACE_EINVAL, "ctx is NULL");
+    if (tile_x) *tile_x = TILE_X;
+    if (rows_per_cta) *rows_per_cta = c->rows;
+    if (grid_x) *grid_x = c->grid_x;
+    if (grid_y) *grid_y = c->grid_y;
+    return LBM_ACE_OK;
+}
+
+int lbm_ace_synchronize(lbm_ace_ctx* c)
+{
+    if (!c) return fail(nullptr, LBM_ACE_EINVAL, "ctx is NULL");
+    DeviceGuard g(c->dev);
+    CK(c, cudaStreamSynchronize(c->stream));
+    return LBM_ACE_OK;
+}
+
+} // extern "C"

@@ -1,0 +1,275 @@
+"""Python binding of the C ABI in include/lbm_ace.h (argument marshalling only).
+
+Every function here forwards to the entry point of the same name in
+``liblbm_ace.so``; all lattice Boltzmann arithmetic runs in the library's CUDA
+kernels. There is no CPU fallback: if the library cannot be loaded, every call
+raises. PyTorch is optional and only used to hand in a CUDA stream or to
+receive arrays as tensors.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+# status codes
+OK, EINVAL, ENOMEM, ECUDA, ENUMERIC, ETIMEOUT, ECALLBACK = 0, -1, -2, -3, -4, -5, -6
+# precision
+F64, F32, F16DEV, BF16DEV = 0, 1, 2, 3
+# model
+MODEL_MODIFIED, MODEL_CONSERVATIVE = 0, 1
+# velocity
+VEL_SINGLE_VORTEX, VEL_UNIFORM, VEL_FIELD, VEL_CALLBACK = 0, 1, 2, 3
+
+VELOCITY_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                               ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                               ctypes.c_void_p)
+
+# Entry points declared in include/lbm_ace.h (checked by the test suite).
+EXPORTS = (
+    "lbm_ace_params_default", "lbm_ace_init", "lbm_ace_step", "lbm_ace_get_phi", "lbm_ace_mass",
+    "lbm_ace_step_mass", "lbm_ace_get_state", "lbm_ace_set_state", "lbm_ace_steps_done",
+    "lbm_ace_launch_shape", "lbm_ace_synchronize", "lbm_ace_last_error", "lbm_ace_status_string",
+    "lbm_ace_destroy",
+)
+
+
+class lbm_ace_params(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int), ("ny", ctypes.c_int),
+        ("tau", ctypes.c_double), ("M", ctypes.c_double), ("eps", ctypes.c_double),
+        ("reg_delta", ctypes.c_double),
+        ("precision", ctypes.c_int), ("model", ctypes.c_int), ("velocity_kind", ctypes.c_int),
+        ("U0", ctypes.c_double), ("T_period", ctypes.c_double), ("vortex_sign", ctypes.c_double),
+        ("ux", ctypes.c_double), ("uy", ctypes.c_double),
+        ("u_field", ctypes.POINTER(ctypes.c_double)), ("v_field", ctypes.POINTER(ctypes.c_double)),
+        ("vel_fn", VELOCITY_FN), ("vel_user", ctypes.c_void_p),
+        ("phi0", ctypes.POINTER(ctypes.c_double)),
+        ("xc", ctypes.c_double), ("yc", ctypes.c_double), ("R", ctypes.c_double),
+        ("device", ctypes.c_int), ("stream", ctypes.c_void_p),
+        ("rows_per_cta", ctypes.c_int),
+    ]
+
+
+class LbmAceError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{message} [status {status}]")
+        self.status = status
+
+
+_lib = None
+_D = ctypes.POINTER(ctypes.c_double)
+_P = ctypes.c_void_p
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load liblbm_ace.so (compiling it with nvcc if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing and not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(path):
+        raise LbmAceError(ECUDA, f"CUDA library {path} is missing; run __graft_entry__.build()")
+    L = ctypes.CDLL(path)
+    L.lbm_ace_params_default.argtypes = [ctypes.POINTER(lbm_ace_params)]
+    L.lbm_ace_init.argtypes = [ctypes.POINTER(lbm_ace_params), ctypes.POINTER(_P)]
+    L.lbm_ace_step.argtypes = [_P, ctypes.c_longlong]
+    L.lbm_ace_get_phi.argtypes = [_P, _D, ctypes.c_size_t]
+    L.lbm_ace_mass.argtypes = [_P, _D]
+    L.lbm_ace_step_mass.argtypes = [_P, _D]
+    L.lbm_ace_get_state.argtypes = [_P, _D, _D]
+    L.lbm_ace_set_state.argtypes = [_P, _D, _D, ctypes.c_longlong]
+    L.lbm_ace_steps_done.argtypes = [_P]
+    L.lbm_ace_steps_done.restype = ctypes.c_longlong
+    L.lbm_ace_launch_shape.argtypes = [_P] + [ctypes.POINTER(ctypes.c_int)] * 4
+    L.lbm_ace_synchronize.argtypes = [_P]
+    L.lbm_ace_last_error.argtypes = [_P]
+    L.lbm_ace_last_error.restype = ctypes.c_char_p
+    L.lbm_ace_status_string.argtypes = [ctypes.c_int]
+    L.lbm_ace_status_string.restype = ctypes.c_char_p
+    L.lbm_ace_destroy.argtypes = [_P]
+    L.lbm_ace_destroy.restype = None
+    for name in ("lbm_ace_params_default", "lbm_ace_init", "lbm_ace_step", "lbm_ace_get_phi",
+                 "lbm_ace_mass", "lbm_ace_step_mass", "lbm_ace_get_state", "lbm_ace_set_state",
+                 "lbm_ace_launch_shape", "lbm_ace_synchronize"):
+        getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(_D)
+
+
+def params_default() -> lbm_ace_params:
+    p = lbm_ace_params()
+    load().lbm_ace_params_default(ctypes.byref(p))
+    return p
+
+
+def _check(ctx, rc: int):
+    if rc != OK:
+        msg = load().lbm_ace_last_error(ctx)
+        raise LbmAceError(rc, (msg or b"").decode(errors="replace"))
+
+
+class Lattice:
+    """One lattice owned by the library (wraps lbm_ace_init ... lbm_ace_destroy).
+
+    Keyword arguments set fields of ``lbm_ace_params`` (same names); ``phi0``,
+    ``u_field`` and ``v_field`` take float64 arrays of shape [ny, nx];
+    ``stream`` takes a CUDA stream handle (int) or a ``torch.cuda.Stream``;
+    ``vel_fn`` takes a Python callable ``f(t, nx, ny) -> (u, v)``."""
+
+    def __init__(self, **kw):
+        self._lib = load()
+        p = params_default()
+        self._keep = []
+        for k in ("phi0", "u_field", "v_field"):
+            a = kw.pop(k, None)
+            if a is not None:
+                arr = np.ascontiguousarray(a, dtype=np.float64)
+                self._keep.append(arr)
+                setattr(p, k, _dp(arr))
+        stream = kw.pop("stream", None)
+        if stream is not None:
+            p.stream = ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+        fn = kw.pop("vel_fn", None)
+        if fn is not None:
+            def tramp(t, nx, ny, u, v, user, _fn=fn):
+                try:
+                    uu, vv = _fn(t, nx, ny)
+                    n = nx * ny
+                    np.ctypeslib.as_array(u, (n,))[:] = np.asarray(uu, dtype=np.float64).ravel()
+                    np.ctypeslib.as_array(v, (n,))[:] = np.asarray(vv, dtype=np.float64).ravel()
+                    return 0
+                except Exception:  # reported to the caller as LBM_ACE_ECALLBACK
+                    return 1
+            cb = VELOCITY_FN(tramp)
+            self._keep.append(cb)
+            p.vel_fn = cb
+            p.velocity_kind = VEL_CALLBACK
+        for k, v in kw.items():
+            if not hasattr(p, k):
+                raise TypeError(f"unknown parameter {k!r}")
+            setattr(p, k, v)
+        self.params = p
+        self.nx, self.ny = p.nx, p.ny
+        ctx = _P()
+        rc = self._lib.lbm_ace_init(ctypes.byref(p), ctypes.byref(ctx))
+        if rc != OK:
+            raise LbmAceError(rc, (self._lib.lbm_ace_last_error(None) or b"").decode(errors="replace"))
+        self.ctx = ctx
+
+    # -- C ABI, one method per entry point --------------------------------------
+    def lbm_ace_step(self, n: int = 1) -> "Lattice":
+        _check(self.ctx, self._lib.lbm_ace_step(self.ctx, int(n)))
+        return self
+
+    step = lbm_ace_step
+
+    def lbm_ace_get_phi(self, out: Optional[np.ndarray] = None) -> np.ndarray:
+        if out is None:
+            out = np.empty((self.ny, self.nx), dtype=np.float64)
+        assert out.dtype == np.float64 and out.flags.c_contiguous and out.size == self.nx * self.ny
+        _check(self.ctx, self._lib.lbm_ace_get_phi(self.ctx, _dp(out), out.size))
+        return out
+
+    phi = lbm_ace_get_phi
+
+    def lbm_ace_mass(self) -> float:
+        m = ctypes.c_double()
+        _check(self.ctx, self._lib.lbm_ace_mass(self.ctx, ctypes.byref(m)))
+        return m.value
+
+    mass = lbm_ace_mass
+
+    def lbm_ace_step_mass(self) -> float:
+        m = ctypes.c_double()
+        _check(self.ctx, self._lib.lbm_ace_step_mass(self.ctx, ctypes.byref(m)))
+        return m.value
+
+    step_mass = lbm_ace_step_mass
+
+    def lbm_ace_get_state(self):
+        f = np.empty((9, self.ny, self.nx), dtype=np.float64)
+        pp = np.empty((self.ny, self.nx), dtype=np.float64)
+        _check(self.ctx, self._lib.lbm_ace_get_state(self.ctx, _dp(f), _dp(pp)))
+        return f, pp
+
+    get_state = lbm_ace_get_state
+
+    def lbm_ace_set_state(self, f: np.ndarray, phi_prev: np.ndarray, t: int) -> "Lattice":
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        pp = np.ascontiguousarray(phi_prev, dtype=np.float64)
+        assert f.size == 9 * self.nx * self.ny and pp.size == self.nx * self.ny
+        _check(self.ctx, self._lib.lbm_ace_set_state(self.ctx, _dp(f), _dp(pp), int(t)))
+        return self
+
+    set_state = lbm_ace_set_state
+
+    def lbm_ace_steps_done(self) -> int:
+        return int(self._lib.lbm_ace_steps_done(self.ctx))
+
+    @property
+    def t(self) -> int:
+        return self.lbm_ace_steps_done()
+
+    def lbm_ace_launch_shape(self):
+        v = [ctypes.c_int() for _ in range(4)]
+        _check(self.ctx, self._lib.lbm_ace_launch_shape(self.ctx, *[ctypes.byref(x) for x in v]))
+        return tuple(x.value for x in v)
+
+    launch_shape = lbm_ace_launch_shape
+
+    def lbm_ace_synchronize(self) -> None:
+        _check(self.ctx, self._lib.lbm_ace_synchronize(self.ctx))
+
+    synchronize = lbm_ace_synchronize
+
+    def close(self) -> None:
+        if getattr(self, "ctx", None):
+            self._lib.lbm_ace_destroy(self.ctx)
+            self.ctx = None
+
+    lbm_ace_destroy = close
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def status_string(rc: int) -> str:
+    return load().lbm_ace_status_string(rc).decode()
+
+
+def vortex_lattice(L: int, *, eps: float = 1.0, tau: float = 0.8, U0: float = 0.04,
+                   T: float = None, precision: int = F32, R_frac: float = 0.15,
+                   xc_frac: float = 0.5, yc_frac: float = 0.75, sign: float = -1.0,
+                   **kw) -> Lattice:
+    """The single-vortex workload (Section 3, Eq. 14) with the disk built by the library."""
+    return Lattice(nx=L, ny=L, tau=tau, eps=eps, U0=U0, T_period=float(T if T else 16 * L),
+                   vortex_sign=sign, precision=precision, velocity_kind=VEL_SINGLE_VORTEX,
+                   xc=xc_frac * L, yc=yc_frac * L, R=R_frac * L, **kw)
+
+
+DEFAULT_DELTA = math.exp(-20.0)
