@@ -13,7 +13,8 @@
 //   a7 velocity           Eq. 14 from separable 1-D tables (no memory traffic per node)
 //   a8 time derivative    d_t(phi u) = phi(t) u(t) - phi(t-1) u(t-1)   (explicit Euler)
 //   a9 forcing            F_i = w_i c_i . (d_t(phi u) + c_s^2 S n) / c_s^2   (Eq. 11)
-//   a10 equilibrium       f_i^eq = w_i phi (1 + c_i . u / c_s^2)       (Eq. 10)
+//   a10 equilibrium       f_i^eq = w_i phi (1 + c_i . u / c_s^2)       (Eq. 10), f_0^eq as
+//                           the remainder phi - sum_{i>=1} f_i^eq (exact mass in any precision)
 //   a11 collision         f*_i = f_i - (f_i - f_i^eq)/tau + (1 - 1/(2 tau)) F_i  (Eq. 9)
 //   a12 store             f*_i (SoA planes) and phi(t) (becomes phi(t-1) of the next step)
 //   a13 mass partial      one FP64 sum of phi per CTA
@@ -117,6 +118,24 @@ struct VelPlanes { // device FP64 planes of u(t), v(t), u(t-1), v(t-1)
         uu = T(u[k]); vv = T(v[k]); upp = T(up[k]); vpp = T(vp[k]);
     }
 };
+
+// Eq. 10, f_i^eq = w_i phi (1 + c_i . u / c_s^2), with f_0^eq taken as the remainder
+// phi - sum_{i>=1} f_i^eq. Since c_0 = 0 this equals w_0 phi in real arithmetic; in
+// floating point it makes the equilibrium carry exactly the mass phi whatever the
+// rounding of the weights (in FP32 the nine weights sum to 1 + 7.5e-9, which would add
+// omega * phi * 7.5e-9 of mass at every node and step).
+template <typename T>
+__device__ __forceinline__ void equilibrium(T ph, T u, T v, T* feq)
+{
+    T rest = T(0);
+#pragma unroll
+    for (int i = 1; i < 9; ++i) {
+        const T cu = T(cx_of(i)) * u + T(cy_of(i)) * v;
+        feq[i] = w_of<T>(i) * ph * (T(1) + T(3) * cu);
+        rest += feq[i];
+    }
+    feq[0] = ph - rest;
+}
 
 // chi is the field whose isotropic gradient gives the normal: psi (Eq. 13) for the
 // paper's model, phi for the conservative-ACE ablation (Eq. 1).
@@ -249,14 +268,14 @@ __global__ void __launch_bounds__(TILE_X) ace_step(const StepArgs<T> a, const Ve
             const T Gx = dx + S * nxv * third; // bracket of Eq. 11: d_t(phi u) + c_s^2 S n
             const T Gy = dy + S * nyv * third;
             const T om1 = T(1) - a.omega;
+            T feq[9];
+            equilibrium(phb, u, v, feq);
             T* o = a.fout + (long long)yc * a.nx + x;
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
-                const T cu = T(cx_of(i)) * u + T(cy_of(i)) * v;
                 const T cg = T(cx_of(i)) * Gx + T(cy_of(i)) * Gy;
-                const T feq = w_of<T>(i) * phb * (T(1) + T(3) * cu);
                 const T F = T(3) * w_of<T>(i) * cg;
-                o[(long long)i * a.plane] = fb[i] * om1 + a.omega * feq + a.fpref * F;
+                o[(long long)i * a.plane] = fb[i] * om1 + a.omega * feq[i] + a.fpref * F;
             }
             *phr = phb;
             msum += (double)phb;
@@ -279,8 +298,9 @@ __global__ void __launch_bounds__(TILE_X) ace_step(const StepArgs<T> a, const Ve
     }
 }
 
-// Initial state (R7): f_i(x, 0) = f_i^eq(phi0(x), u(x, 0)). Stored as the post-
-// collision buffer f*(-1) from which the first step pulls: f*_i(x) = f_i(x + c_i, 0).
+// Initial state: f_i(x, 0) = f_i^eq(phi0(x), u(x, 0)). Stored as the post-collision
+// buffer f*(-1) from which the first step pulls, f*_i(x - c_i) = f_i(x, 0): each node
+// pushes its 9 equilibria to x - c_i.
 template <typename T, class Vel>
 __global__ void ace_init(const double* __restrict__ phi0, T* __restrict__ fst, T* __restrict__ phi,
                          int nx, int ny, Vel vel)
@@ -289,16 +309,14 @@ __global__ void ace_init(const double* __restrict__ phi0, T* __restrict__ fst, T
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < plane;
          k += (long long)gridDim.x * blockDim.x) {
         const int x = (int)(k % nx), y = (int)(k / nx);
+        const T ph = T(phi0[k]);
+        T u, v, up, vp, feq[9];
+        vel.at(vel.col(x), x, y, u, v, up, vp);
+        equilibrium(ph, u, v, feq);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            const int sx = wrap_idx(x + cx_of(i), nx), sy = wrap_idx(y + cy_of(i), ny);
-            const T ph = T(phi0[(long long)sy * nx + sx]);
-            T u, v, up, vp;
-            vel.at(vel.col(sx), sx, sy, u, v, up, vp);
-            const T cu = T(cx_of(i)) * u + T(cy_of(i)) * v;
-            fst[i * plane + k] = w_of<T>(i) * ph * (T(1) + T(3) * cu);
-        }
-        phi[k] = T(phi0[k]);
+        for (int i = 0; i < 9; ++i)
+            fst[i * plane + (long long)wrap_idx(y - cy_of(i), ny) * nx + wrap_idx(x - cx_of(i), nx)] = feq[i];
+        phi[k] = ph;
     }
 }
 
