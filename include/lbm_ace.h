@@ -166,6 +166,34 @@ int lbm_ace_launch_shape(const lbm_ace_ctx* c, int* tile_x, int* rows_per_cta, i
 /* Block until all device work of the context has finished. */
 int lbm_ace_synchronize(lbm_ace_ctx* c);
 
+/* Allocation-free global mass, for callers that cannot allocate device memory (the
+ * paper has no counterpart; it is a service of this library). Some callers cannot
+ * call cudaMalloc: their device memory is already handed out by their own pool or
+ * caching allocator, or their time-critical loop cannot take the implicit device
+ * synchronisation that cudaMalloc/cudaFree may bring. They pass their own buffers:
+ *   values   device address of `count` values, FP64 (precision LBM_ACE_F64) or FP32
+ *            (LBM_ACE_F32), e.g. the 9 population planes of a lattice or a phi field;
+ *   out      device address of one double that receives the sum (the same
+ *            compensated, fixed-order summation as lbm_ace_mass; 0 for count == 0);
+ *   stream   cudaStream_t of the current device (NULL: legacy default stream).
+ * The work is asynchronous on `stream` and runs on the current CUDA device.
+ * Scratch: the per-chunk partial sums live in a fixed array of static device memory
+ * inside the library, LBM_ACE_NOALLOC_MAX_PARTIALS doubles (32 KiB), present on every
+ * GPU that loads the library until the process exits. Each call overwrites the slots
+ * it uses, so nothing carries over between calls. Because every call shares that one
+ * array, calls whose work can overlap on the GPU (other streams, other threads)
+ * race and may return wrong sums: order them on one stream or synchronise.
+ * The first call on a device looks up the array's device address for that device
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Limits: count <= LBM_ACE_NOALLOC_MAX_COUNT (268,435,456 values); a larger count,
+ * a NULL pointer or another precision returns LBM_ACE_EINVAL without device work.
+ * Calls no cudaMalloc, cudaFree or other allocating routine. Returns LBM_ACE_ECUDA
+ * when a launch or the address lookup fails. */
+#define LBM_ACE_NOALLOC_CHUNK 65536
+#define LBM_ACE_NOALLOC_MAX_PARTIALS 4096
+#define LBM_ACE_NOALLOC_MAX_COUNT (65536LL * 4096LL)
+int lbm_ace_mass_noalloc(const void* values, int precision, long long count, double* out, void* stream);
+
 const char* lbm_ace_last_error(const lbm_ace_ctx* c);
 const char* lbm_ace_status_string(int status);
 

@@ -35,8 +35,11 @@ EXPORTS = (
     "lbm_ace_params_default", "lbm_ace_init", "lbm_ace_step", "lbm_ace_get_phi", "lbm_ace_mass",
     "lbm_ace_step_mass", "lbm_ace_get_state", "lbm_ace_set_state", "lbm_ace_steps_done",
     "lbm_ace_launch_shape", "lbm_ace_synchronize", "lbm_ace_last_error", "lbm_ace_status_string",
-    "lbm_ace_destroy",
+    "lbm_ace_destroy", "lbm_ace_mass_noalloc",
 )
+NOALLOC_CHUNK = 65536
+NOALLOC_MAX_PARTIALS = 4096
+NOALLOC_MAX_COUNT = NOALLOC_CHUNK * NOALLOC_MAX_PARTIALS
 
 
 class lbm_ace_params(ctypes.Structure):
@@ -100,6 +103,8 @@ def load(build_if_missing: bool = True):
     L.lbm_ace_status_string.restype = ctypes.c_char_p
     L.lbm_ace_destroy.argtypes = [_P]
     L.lbm_ace_destroy.restype = None
+    L.lbm_ace_mass_noalloc.argtypes = [_P, ctypes.c_int, ctypes.c_longlong, _P, _P]
+    L.lbm_ace_mass_noalloc.restype = ctypes.c_int
     for name in ("lbm_ace_params_default", "lbm_ace_init", "lbm_ace_step", "lbm_ace_get_phi",
                  "lbm_ace_mass", "lbm_ace_step_mass", "lbm_ace_get_state", "lbm_ace_set_state",
                  "lbm_ace_launch_shape", "lbm_ace_synchronize"):
@@ -256,6 +261,16 @@ class Lattice:
 
     def __exit__(self, *a):
         self.close()
+
+
+def lbm_ace_mass_noalloc(values_ptr: int, precision: int, count: int, out_ptr: int,
+                         stream: int = 0) -> int:
+    """Allocation-free global mass of `count` device values (FP64 or FP32) into the device
+    double at `out_ptr`, asynchronous on `stream`; returns the status code. For callers
+    that cannot allocate device memory: the library keeps its partial sums in a fixed
+    static device array, so overlapping calls on the GPU race (see include/lbm_ace.h)."""
+    return int(load().lbm_ace_mass_noalloc(_P(values_ptr), int(precision), int(count),
+                                           _P(out_ptr), _P(int(getattr(stream, "cuda_stream", stream)))))
 
 
 def status_string(rc: int) -> str:
