@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--L", type=int, default=2048)
     ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
     ap.add_argument("--rows", type=int, default=0, help="rows per CTA (0: library default)")
+    ap.add_argument("--variant", type=int, default=0, help="step kernel: 0 auto, 1 direct loads, 2 bulk-copy pipeline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -135,15 +136,22 @@ def rejected(clk):
     return False
 
 
-def stored_traffic(precision: str, L: int):
+def kernel_source_hash() -> str:
+    """Hash of the step kernels' device sources (both variants)."""
+    h = hashlib.sha256()
+    for name in ("ace_kernels.cuh", "ace_step_bulk.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2203_05230_gb300", "csrc", name), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def stored_traffic(kernel: str, precision: str, L: int):
     """DRAM bytes per launch of the fused step from the committed ncu summary, or None
     when the kernel source has changed since the counters were taken."""
-    path = os.path.join(ROOT, "profiles", f"ace_step_{precision}_{L}.json")
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{precision}_{L}.json")
     if not os.path.exists(path):
         return None
     d = json.load(open(path))
-    src = os.path.join(ROOT, "paper_2203_05230_gb300", "csrc", "ace_kernels.cuh")
-    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    h = kernel_source_hash()
     if d.get("kernel_source_sha256_16") != h:
         return None
     return d.get("dram_bytes_per_launch")
@@ -227,7 +235,8 @@ def run_ours(args):
     prec = {"f32": A.F32, "f64": A.F64}[args.precision]
     stream = torch.cuda.current_stream()
     lat = A.vortex_lattice(args.L, eps=v.eps, tau=v.tau, U0=v.U0, T=v.T, precision=prec,
-                           stream=stream.cuda_stream, device=dev, rows_per_cta=args.rows)
+                           stream=stream.cuda_stream, device=dev, rows_per_cta=args.rows,
+                           kernel_variant=args.variant)
     shape = lat.launch_shape()
     for _ in range(args.warmup):
         lat.step(1)
@@ -268,7 +277,7 @@ def run_ours(args):
     bpl = BYTES_PER_LUP[args.precision] * args.L * args.L
     peak, peak_kind = measured_peak()
     achieved = bpl / per_launch / 1e9
-    traffic = stored_traffic(args.precision, args.L)
+    traffic = stored_traffic("ace_step_bulk" if shape[4] == 2 else "ace_step", args.precision, args.L)
     lat.close()
 
     e2e = None
@@ -279,13 +288,16 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": per_launch * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
             "config": {**cfg, "launch": {"tile_x": shape[0], "rows_per_cta": shape[1],
-                                         "grid": [shape[2], shape[3]]},
+                                         "grid": [shape[2], shape[3]],
+                                         "kernel": {1: "ace_step (direct loads)",
+                                                    2: "ace_step_bulk (bulk-copy pipeline)"}[shape[4]]},
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                          else "fallback",
-                         "algorithmic_bytes_per_launch": bpl, "kernel": "lbmace::ace_step"},
+                         "algorithmic_bytes_per_launch": bpl,
+                         "kernel": "lbmace::ace_step_bulk" if shape[4] == 2 else "lbmace::ace_step"},
             "hbm_gbs_algorithmic": achieved,
             "mass_drift_rel_timed": (m1 - m0) / m0,
             "clocks": clk, "gpu_launches": args.steps, "e2e": e2e}
@@ -312,7 +324,7 @@ def run_e2e(args, v, prec, stream, dev, A):
     t0 = time.perf_counter()
     lat = A.Lattice(nx=args.L, ny=args.L, tau=v.tau, eps=v.eps, U0=v.U0, T_period=float(v.T),
                     vortex_sign=v.sign, precision=prec, stream=stream.cuda_stream, device=dev,
-                    phi0=phi0.numpy(), rows_per_cta=args.rows)
+                    phi0=phi0.numpy(), rows_per_cta=args.rows, kernel_variant=args.variant)
     lat.step(args.steps)
     lat.phi(out.numpy().reshape(args.L, args.L))
     m = lat.mass()

@@ -19,9 +19,10 @@
  *    next call on the same context (or, for NULL, on the same thread).
  *  - Host pointers are owned by the caller and are only read or written
  *    during the call. The context owns its device memory.
- *  - All device work is issued on the stream given at init. lbm_ace_step and
- *    lbm_ace_step_async return without waiting; the functions that return
- *    values to the host synchronise that stream first.
+ *  - All device work is issued on the stream given at init. lbm_ace_step
+ *    returns without waiting; the functions that return values to the host
+ *    synchronise that stream first and then report LBM_ACE_ETIMEOUT if a
+ *    bounded wait inside a kernel gave up since the last such report.
  *  - Arrays are row-major: a scalar field is [ny][nx] with x fastest; a
  *    population field is [9][ny][nx] in the D2Q9 order c_0 = (0,0),
  *    c_1..c_4 = (1,0), (0,1), (-1,0), (0,-1), c_5..c_8 = (1,1), (-1,1),
@@ -115,6 +116,10 @@ typedef struct lbm_ace_params {
     void* stream;        /* cudaStream_t for all device work; NULL = the legacy default stream */
     int rows_per_cta;    /* launch shape of the fused step: rows each CTA marches over;
                             0 selects a default for the lattice size and the device */
+    int kernel_variant;  /* fused step kernel: 0 = automatic, 1 = direct global loads,
+                            2 = rows staged in shared memory by bulk copies (needs
+                            nx * element size a multiple of 16 bytes). Both give
+                            bit-identical results. */
 } lbm_ace_params;
 
 typedef struct lbm_ace_ctx lbm_ace_ctx; /* opaque; owns its device buffers */
@@ -160,8 +165,10 @@ int lbm_ace_set_state(lbm_ace_ctx* c, const double* f, const double* phi_prev, l
 /* Current time t (number of steps taken since init, or as set). */
 long long lbm_ace_steps_done(const lbm_ace_ctx* c);
 
-/* Rows per CTA chosen for the fused step (the launch shape). */
-int lbm_ace_launch_shape(const lbm_ace_ctx* c, int* tile_x, int* rows_per_cta, int* grid_x, int* grid_y);
+/* Launch shape chosen for the fused step: columns and rows per CTA, grid, and the
+ * kernel variant (1 or 2, see lbm_ace_params.kernel_variant). Any pointer may be NULL. */
+int lbm_ace_launch_shape(const lbm_ace_ctx* c, int* tile_x, int* rows_per_cta, int* grid_x, int* grid_y,
+                         int* kernel_variant);
 
 /* Block until all device work of the context has finished. */
 int lbm_ace_synchronize(lbm_ace_ctx* c);

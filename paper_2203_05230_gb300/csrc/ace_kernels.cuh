@@ -13,9 +13,10 @@
 //   a7 velocity           Eq. 14 from separable 1-D tables (no memory traffic per node)
 //   a8 time derivative    d_t(phi u) = phi(t) u(t) - phi(t-1) u(t-1)   (explicit Euler)
 //   a9 forcing            F_i = w_i c_i . (d_t(phi u) + c_s^2 S n) / c_s^2   (Eq. 11)
-//   a10 equilibrium       f_i^eq = w_i phi (1 + c_i . u / c_s^2)       (Eq. 10), f_0^eq as
-//                           the remainder phi - sum_{i>=1} f_i^eq (exact mass in any precision)
-//   a11 collision         f*_i = f_i - (f_i - f_i^eq)/tau + (1 - 1/(2 tau)) F_i  (Eq. 9)
+//   a10 equilibrium       f_i^eq = w_i phi (1 + c_i . u / c_s^2)       (Eq. 10)
+//   a11 collision         f*_i = f_i - (f_i - f_i^eq)/tau + (1 - 1/(2 tau)) F_i  (Eq. 9),
+//                           evaluated as (1 - 1/tau) f_i + w_i (A + c_i . B) with f*_0 the
+//                           remainder phi - sum_{i>=1} f*_i (exact mass in any precision)
 //   a12 store             f*_i (SoA planes) and phi(t) (becomes phi(t-1) of the next step)
 //   a13 mass partial      one FP64 sum of phi per CTA
 //
@@ -139,15 +140,96 @@ __device__ __forceinline__ void equilibrium(T ph, T u, T v, T* feq)
 
 // chi is the field whose isotropic gradient gives the normal: psi (Eq. 13) for the
 // paper's model, phi for the conservative-ACE ablation (Eq. 1).
+// psi of Eq. 13 from the clipped phi. FP64: one log of the ratio. FP32: the hardware
+// base-2 logarithm of numerator and denominator (no division); its ~1e-7 absolute
+// error in psi only perturbs the direction of n, far below FP32 storage rounding.
+__device__ __forceinline__ double psi_clipped(double pc, double eps, double delta)
+{
+    return eps * log((pc + delta) / (1.0 - pc + delta));
+}
+__device__ __forceinline__ float psi_clipped(float pc, float eps, float delta)
+{
+    return (eps * 0.69314718055994531f) * (__log2f(pc + delta) - __log2f(1.0f - pc + delta));
+}
+
+// 1 / (|g| + delta) for the normal of Eq. 13. FP32 uses the hardware reciprocal square
+// root and reciprocal (the normal's direction, not its last bits, enters Eq. 11).
+__device__ __forceinline__ double inv_norm(double g2, double delta) { return 1.0 / (sqrt(g2) + delta); }
+__device__ __forceinline__ float inv_norm(float g2, float delta)
+{
+    const float g = g2 > 0.0f ? g2 * rsqrtf(g2) : 0.0f;
+    return __fdividef(1.0f, g + delta);
+}
+
 template <typename T, int MODEL>
 __device__ __forceinline__ T chi_of(T ph, const StepArgs<T>& a)
 {
     if (MODEL == MODEL_MODIFIED) {
         const T pc = ph < T(0) ? T(0) : (ph > T(1) ? T(1) : ph);
-        return a.eps * dlog((pc + a.delta) / (T(1) - pc + a.delta));
+        return psi_clipped(pc, a.eps, a.delta);
     } else {
         return ph;
     }
+}
+
+// Steps a4-a12 for one node (x, yc): gradient of chi from the three stencil rows
+// (cS/cC/cN point at column x - 1 of rows yc - 1, yc, yc + 1), normal, sharpening,
+// velocity, time derivative, forcing, equilibrium, BGK, and the 9 stores of f*.
+// f: pulled populations f_i(x, t); ph = phi(x, t); pp = phi(x, t - 1).
+template <typename T, int MODEL, class Vel>
+__device__ __forceinline__ void collide_node(const StepArgs<T>& a, const Vel& vel, const typename Vel::Col& vcol,
+                                             int x, int yc, const T* f, T ph, T pp,
+                                             const T* cS, const T* cC, const T* cN)
+{
+    const T third = T(1) / T(3), twelfth = T(1) / T(12);
+    // 3 sum_i w_i c_i chi(x + c_i): axis neighbours weigh 3/9, diagonals 3/36
+    const T gx = (cC[2] - cC[0]) * third + ((cN[2] - cN[0]) + (cS[2] - cS[0])) * twelfth;
+    const T gy = (cN[1] - cS[1]) * third + ((cN[2] + cN[0]) - (cS[2] + cS[0])) * twelfth;
+    const T inv = inv_norm(gx * gx + gy * gy, a.delta);
+    const T nxv = gx * inv, nyv = gy * inv;
+    T S;
+    if (MODEL == MODEL_MODIFIED) {
+        const T pc = ph < T(0) ? T(0) : (ph > T(1) ? T(1) : ph);
+        const T th = (T(2) * pc - T(1)) * a.inv1p2d;
+        S = (T(1) - th * th) * a.inv4eps;
+    } else {
+        S = ph * (T(1) - ph) * a.inv_eps;
+    }
+    T u, v, up, vp;
+    vel.at(vcol, x, yc, u, v, up, vp);
+    T dx = T(0), dy = T(0);
+    if (!a.first) {
+        dx = ph * u - pp * up;
+        dy = ph * v - pp * vp;
+    }
+    const T Gx = dx + S * nxv * third; // bracket of Eq. 11: d_t(phi u) + c_s^2 S n
+    const T Gy = dy + S * nyv * third;
+    // Eqs. 9-11 folded: f*_i = (1 - omega) f_i + w_i (A + c_i . B) with A = omega phi
+    // and B = 3 (omega phi u + (1 - 1/(2 tau)) G); f*_0 is the remainder phi - sum_{i>=1}
+    // f*_i (sum_i f*_i = phi holds exactly in real arithmetic), so the collision
+    // conserves mass in any precision whatever the rounding of the weights.
+    const T om1 = T(1) - a.omega;
+    const T A = a.omega * ph;
+    const T Bx = T(3) * (A * u + a.fpref * Gx);
+    const T By = T(3) * (A * v + a.fpref * Gy);
+    const T w1 = w_of<T>(1), w5 = w_of<T>(5);
+    T fs[9];
+    fs[1] = f[1] * om1 + w1 * (A + Bx);
+    fs[2] = f[2] * om1 + w1 * (A + By);
+    fs[3] = f[3] * om1 + w1 * (A - Bx);
+    fs[4] = f[4] * om1 + w1 * (A - By);
+    const T Bp = Bx + By, Bm = Bx - By;
+    fs[5] = f[5] * om1 + w5 * (A + Bp);
+    fs[6] = f[6] * om1 + w5 * (A - Bm);
+    fs[7] = f[7] * om1 + w5 * (A - Bp);
+    fs[8] = f[8] * om1 + w5 * (A + Bm);
+    T rest = T(0);
+#pragma unroll
+    for (int i = 1; i < 9; ++i) rest += fs[i];
+    fs[0] = ph - rest;
+    T* o = a.fout + (long long)yc * a.nx + x;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) o[(long long)i * a.plane] = fs[i];
 }
 
 // Population i of node (x, y) at time t, pulled from f*(t-1) at (x - c_i, y - c_i).
@@ -203,7 +285,7 @@ __global__ void __launch_bounds__(TILE_X) ace_step(const StepArgs<T> a, const Ve
     T fa[9], fb[9];
     T hv = T(0);
     T phb = T(0);
-    double msum = 0.0;
+    double msum = 0.0; // FP64 column sum of phi over this thread's rows
 
     {
         const int r = wrap_idx(y0 - 1, a.ny);
@@ -239,44 +321,10 @@ __global__ void __launch_bounds__(TILE_X) ace_step(const StepArgs<T> a, const Ve
         if (k >= 2 && act) {
             // Collide row yc = y0 + k - 2 with its pulled populations fb and phi phb.
             const int yc = y0 + k - 2;
-            const T* cS = chi_s[(k - 2) & 3] + tx; // row yc - 1, index +1 = own column
-            const T* cC = chi_s[(k - 1) & 3] + tx; // row yc
-            const T* cN = chi_s[k & 3] + tx;       // row yc + 1
-            const T third = T(1) / T(3), twelfth = T(1) / T(12);
-            // 3 sum_i w_i c_i chi(x + c_i): axis neighbours 3/9, diagonals 3/36
-            const T gx = (cC[2] - cC[0]) * third + ((cN[2] - cN[0]) + (cS[2] - cS[0])) * twelfth;
-            const T gy = (cN[1] - cS[1]) * third + ((cN[2] + cN[0]) - (cS[2] + cS[0])) * twelfth;
-            const T inv = T(1) / (dsqrt(gx * gx + gy * gy) + a.delta);
-            const T nxv = gx * inv, nyv = gy * inv;
-            T S;
-            if (MODEL == MODEL_MODIFIED) {
-                const T pc = phb < T(0) ? T(0) : (phb > T(1) ? T(1) : phb);
-                const T th = (T(2) * pc - T(1)) * a.inv1p2d;
-                S = (T(1) - th * th) * a.inv4eps;
-            } else {
-                S = phb * (T(1) - phb) * a.inv_eps;
-            }
-            T u, v, up, vp;
-            vel.at(vcol, x, yc, u, v, up, vp);
             T* phr = a.phi + (long long)yc * a.nx + x;
-            T dx = T(0), dy = T(0);
-            if (!a.first) {
-                const T pp = *phr;
-                dx = phb * u - pp * up;
-                dy = phb * v - pp * vp;
-            }
-            const T Gx = dx + S * nxv * third; // bracket of Eq. 11: d_t(phi u) + c_s^2 S n
-            const T Gy = dy + S * nyv * third;
-            const T om1 = T(1) - a.omega;
-            T feq[9];
-            equilibrium(phb, u, v, feq);
-            T* o = a.fout + (long long)yc * a.nx + x;
-#pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                const T cg = T(cx_of(i)) * Gx + T(cy_of(i)) * Gy;
-                const T F = T(3) * w_of<T>(i) * cg;
-                o[(long long)i * a.plane] = fb[i] * om1 + a.omega * feq[i] + a.fpref * F;
-            }
+            const T pp = a.first ? T(0) : *phr;
+            collide_node<T, MODEL>(a, vel, vcol, x, yc, fb, phb, pp, chi_s[(k - 2) & 3] + tx,
+                                   chi_s[(k - 1) & 3] + tx, chi_s[k & 3] + tx);
             *phr = phb;
             msum += (double)phb;
         }

@@ -5,6 +5,7 @@
 // and issues one fused step kernel per time step on the caller's stream.
 #include "lbm_ace.h"
 #include "ace_kernels.cuh"
+#include "ace_step_bulk.cuh"
 
 #include <cuda_runtime.h>
 
@@ -53,6 +54,10 @@ struct lbm_ace_ctx {
     long long t = 0;
     bool stepped = false;
     int rows = 0, grid_x = 0, grid_y = 0;
+    int variant = 1;        // 1: ace_step (direct loads), 2: ace_step_bulk
+    int tile_x = TILE_X;
+    size_t smem = 0;        // dynamic shared memory of the chosen step kernel
+    int* dev_err = nullptr; // set by a kernel whose bounded wait gave up
     std::string err;
 };
 
@@ -134,11 +139,18 @@ VelPlanes<T> planes(lbm_ace_ctx* c)
     return v;
 }
 
+constexpr int BULK_TX = 128;
+constexpr int BULK_STAGES = 6;
+
 template <typename T, int MODEL, class Vel>
 void launch_step_k(lbm_ace_ctx* c, const Vel& vel)
 {
     dim3 grid(c->grid_x, c->grid_y);
-    ace_step<T, MODEL, Vel><<<grid, TILE_X, 0, c->stream>>>(make_args<T>(c), vel);
+    if (c->variant == 2)
+        ace_step_bulk<T, MODEL, Vel, BULK_TX, BULK_STAGES>
+            <<<grid, BULK_TX, c->smem, c->stream>>>(make_args<T>(c), vel, c->dev_err);
+    else
+        ace_step<T, MODEL, Vel><<<grid, TILE_X, 0, c->stream>>>(make_args<T>(c), vel);
 }
 
 template <typename T, int MODEL>
@@ -210,27 +222,40 @@ int fill_vortex_tables(lbm_ace_ctx* c)
     return LBM_ACE_OK;
 }
 
+// Occupancy (resident CTAs per SM) of the chosen step kernel; opts the bulk kernel
+// into its dynamic shared memory.
+template <typename T, int MODEL, class Vel>
+int occupancy_k(lbm_ace_ctx* c, int* blocks)
+{
+    if (c->variant == 2) {
+        auto k = ace_step_bulk<T, MODEL, Vel, BULK_TX, BULK_STAGES>;
+        c->smem = sizeof(BulkSmem<T, BULK_TX, BULK_STAGES>);
+        c->tile_x = BULK_TX;
+        CK(c, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem));
+        CK(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k, BULK_TX, c->smem));
+    } else {
+        c->smem = 0;
+        c->tile_x = TILE_X;
+        CK(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, ace_step<T, MODEL, Vel>, TILE_X, 0));
+    }
+    return LBM_ACE_OK;
+}
+
+template <typename T, int MODEL>
+int occupancy_m(lbm_ace_ctx* c, int* blocks)
+{
+    switch (c->p.velocity_kind) {
+    case LBM_ACE_VEL_SINGLE_VORTEX: return occupancy_k<T, MODEL, VelVortex<T>>(c, blocks);
+    case LBM_ACE_VEL_UNIFORM: return occupancy_k<T, MODEL, VelUniform<T>>(c, blocks);
+    default: return occupancy_k<T, MODEL, VelPlanes<T>>(c, blocks);
+    }
+}
+
 template <typename T>
 int occupancy_t(lbm_ace_ctx* c, int* blocks)
 {
-    cudaError_t e;
-    const bool mod = c->p.model == LBM_ACE_MODEL_MODIFIED;
-    switch (c->p.velocity_kind) {
-    case LBM_ACE_VEL_SINGLE_VORTEX:
-        e = mod ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, ace_step<T, MODEL_MODIFIED, VelVortex<T>>, TILE_X, 0)
-                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, ace_step<T, MODEL_CONSERVATIVE, VelVortex<T>>, TILE_X, 0);
-        break;
-    case LBM_ACE_VEL_UNIFORM:
-        e = mod ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, ace_step<T, MODEL_MODIFIED, VelUniform<T>>, TILE_X, 0)
-                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, ace_step<T, MODEL_CONSERVATIVE, VelUniform<T>>, TILE_X, 0);
-        break;
-    default:
-        e = mod ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, ace_step<T, MODEL_MODIFIED, VelPlanes<T>>, TILE_X, 0)
-                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, ace_step<T, MODEL_CONSERVATIVE, VelPlanes<T>>, TILE_X, 0);
-        break;
-    }
-    CK(c, e);
-    return LBM_ACE_OK;
+    return c->p.model == LBM_ACE_MODEL_MODIFIED ? occupancy_m<T, MODEL_MODIFIED>(c, blocks)
+                                                : occupancy_m<T, MODEL_CONSERVATIVE>(c, blocks);
 }
 
 bool is_f64(const lbm_ace_ctx* c) { return c->p.precision == LBM_ACE_F64; }
@@ -259,12 +284,26 @@ int callback_upload(lbm_ace_ctx* c, double t, int pair)
     return LBM_ACE_OK;
 }
 
+int check_device_error(lbm_ace_ctx* c);
+
 int finalize_sum(lbm_ace_ctx* c, const double* part, int n, double* out)
 {
     ace_finalize<<<1, 32, 0, c->stream>>>(part, n, c->result);
     CK(c, cudaGetLastError());
     CK(c, cudaMemcpyAsync(out, c->result, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
+    return check_device_error(c);
+}
+
+// After a stream synchronisation: report (and clear) a bounded wait that gave up.
+int check_device_error(lbm_ace_ctx* c)
+{
+    int e = 0;
+    CK(c, cudaMemcpy(&e, c->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e) {
+        CK(c, cudaMemset(c->dev_err, 0, sizeof(int)));
+        return fail(c, LBM_ACE_ETIMEOUT, "a bounded wait in the step kernel gave up; the state is not valid");
+    }
     return LBM_ACE_OK;
 }
 
@@ -320,7 +359,7 @@ void lbm_ace_destroy(lbm_ace_ctx* c)
     if (!c) return;
     DeviceGuard g(c->dev);
     if (c->stream) cudaStreamSynchronize(c->stream); else cudaDeviceSynchronize();
-    void* bufs[] = {c->f[0], c->f[1], c->phi, c->step_part, c->red_part, c->result, c->scratch,
+    void* bufs[] = {c->f[0], c->f[1], c->phi, c->step_part, c->red_part, c->result, c->scratch, c->dev_err,
                     c->vel.sx2, c->vel.s2x, c->vel.sy2, c->vel.s2y,
                     c->vel.pu[0], c->vel.pu[1], c->vel.pv[0], c->vel.pv[1]};
     for (void* b : bufs) if (b) cudaFree(b);
@@ -344,18 +383,27 @@ static int init_impl(lbm_ace_ctx* c, const lbm_ace_params* p)
     CK(c, cudaMalloc(&c->phi, n * c->elem));
     CK(c, cudaMalloc(&c->result, 2 * sizeof(double)));
 
+    CK(c, cudaMalloc(&c->dev_err, sizeof(int)));
+    CK(c, cudaMemset(c->dev_err, 0, sizeof(int)));
+
+    // kernel variant: the bulk-copy pipeline needs 16-byte aligned rows
+    const bool bulk_ok = ((size_t)nx * c->elem) % 16 == 0;
+    c->variant = p->kernel_variant == 0 ? (bulk_ok ? 2 : 1) : p->kernel_variant;
+
     // launch shape of the fused step: one wave of resident CTAs when possible
     int occ = 0;
     int rc = is_f64(c) ? occupancy_t<double>(c, &occ) : occupancy_t<float>(c, &occ);
     if (rc) return rc;
     if (occ < 1) occ = 1;
-    c->grid_x = (nx + TILE_X - 1) / TILE_X;
+    c->grid_x = (nx + c->tile_x - 1) / c->tile_x;
     int rows = p->rows_per_cta;
     if (rows <= 0) {
+        // one wave: at most `slots` resident CTAs, so at most slots / grid_x row bands
         const long long slots = (long long)c->sms * occ;
-        long long r = ((long long)ny * c->grid_x + slots - 1) / slots;
+        long long bands = slots / c->grid_x;
+        if (bands < 1) bands = 1;
+        long long r = (ny + bands - 1) / bands;
         if (r < 4) r = 4;
-        if (r > 64) r = 64;
         rows = (int)r;
     }
     if (rows > ny) rows = ny;
@@ -455,6 +503,14 @@ int lbm_ace_init(const lbm_ace_params* p, lbm_ace_ctx** out)
         return fail(nullptr, LBM_ACE_EINVAL, "disk centre/radius not finite");
     }
     if (p->rows_per_cta < 0) return fail(nullptr, LBM_ACE_EINVAL, "rows_per_cta must be >= 0");
+    if (p->kernel_variant < 0 || p->kernel_variant > 2)
+        return fail(nullptr, LBM_ACE_EINVAL, "kernel_variant %d unknown", p->kernel_variant);
+    if (p->kernel_variant == 2) {
+        const size_t elem = p->precision == LBM_ACE_F64 ? 8 : 4;
+        if (((size_t)p->nx * elem) % 16 != 0)
+            return fail(nullptr, LBM_ACE_EINVAL, "kernel_variant 2 needs nx * %zu bytes to be a multiple of 16 (nx = %d)",
+                        elem, p->nx);
+    }
     int ndev = 0;
     cudaError_t e = cudaGetDeviceCount(&ndev);
     if (e != cudaSuccess || p->device < 0 || p->device >= ndev)
@@ -510,7 +566,7 @@ int lbm_ace_get_phi(lbm_ace_ctx* c, double* out, size_t count)
     CK(c, cudaGetLastError());
     CK(c, cudaMemcpyAsync(out, c->scratch, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
-    return LBM_ACE_OK;
+    return check_device_error(c);
 }
 
 int lbm_ace_mass(lbm_ace_ctx* c, double* out)
@@ -558,7 +614,7 @@ int lbm_ace_get_state(lbm_ace_ctx* c, double* f, double* phi_prev)
     if (f) CK(c, cudaMemcpyAsync(f, c->scratch, 9 * n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     if (phi_prev) CK(c, cudaMemcpyAsync(phi_prev, c->scratch + 9 * n, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
-    return LBM_ACE_OK;
+    return check_device_error(c);
 }
 
 int lbm_ace_set_state(lbm_ace_ctx* c, const double* f, const double* phi_prev, long long t)
@@ -590,13 +646,15 @@ int lbm_ace_set_state(lbm_ace_ctx* c, const double* f, const double* phi_prev, l
     return LBM_ACE_OK;
 }
 
-int lbm_ace_launch_shape(const lbm_ace_ctx* c, int* tile_x, int* rows_per_cta, int* grid_x, int* grid_y)
+int lbm_ace_launch_shape(const lbm_ace_ctx* c, int* tile_x, int* rows_per_cta, int* grid_x, int* grid_y,
+                         int* kernel_variant)
 {
     if (!c) return fail(nullptr, LBM_ACE_EINVAL, "ctx is NULL");
-    if (tile_x) *tile_x = TILE_X;
+    if (tile_x) *tile_x = c->tile_x;
     if (rows_per_cta) *rows_per_cta = c->rows;
     if (grid_x) *grid_x = c->grid_x;
     if (grid_y) *grid_y = c->grid_y;
+    if (kernel_variant) *kernel_variant = c->variant;
     return LBM_ACE_OK;
 }
 
@@ -605,7 +663,7 @@ int lbm_ace_synchronize(lbm_ace_ctx* c)
     if (!c) return fail(nullptr, LBM_ACE_EINVAL, "ctx is NULL");
     DeviceGuard g(c->dev);
     CK(c, cudaStreamSynchronize(c->stream));
-    return LBM_ACE_OK;
+    return check_device_error(c);
 }
 
 } // extern "C"

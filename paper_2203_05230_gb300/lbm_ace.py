@@ -25,6 +25,8 @@ F64, F32, F16DEV, BF16DEV = 0, 1, 2, 3
 MODEL_MODIFIED, MODEL_CONSERVATIVE = 0, 1
 # velocity
 VEL_SINGLE_VORTEX, VEL_UNIFORM, VEL_FIELD, VEL_CALLBACK = 0, 1, 2, 3
+# fused step kernel variant
+KERNEL_AUTO, KERNEL_DIRECT, KERNEL_BULK = 0, 1, 2
 
 VELOCITY_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
@@ -55,7 +57,7 @@ class lbm_ace_params(ctypes.Structure):
         ("phi0", ctypes.POINTER(ctypes.c_double)),
         ("xc", ctypes.c_double), ("yc", ctypes.c_double), ("R", ctypes.c_double),
         ("device", ctypes.c_int), ("stream", ctypes.c_void_p),
-        ("rows_per_cta", ctypes.c_int),
+        ("rows_per_cta", ctypes.c_int), ("kernel_variant", ctypes.c_int),
     ]
 
 
@@ -95,7 +97,7 @@ def load(build_if_missing: bool = True):
     L.lbm_ace_set_state.argtypes = [_P, _D, _D, ctypes.c_longlong]
     L.lbm_ace_steps_done.argtypes = [_P]
     L.lbm_ace_steps_done.restype = ctypes.c_longlong
-    L.lbm_ace_launch_shape.argtypes = [_P] + [ctypes.POINTER(ctypes.c_int)] * 4
+    L.lbm_ace_launch_shape.argtypes = [_P] + [ctypes.POINTER(ctypes.c_int)] * 5
     L.lbm_ace_synchronize.argtypes = [_P]
     L.lbm_ace_last_error.argtypes = [_P]
     L.lbm_ace_last_error.restype = ctypes.c_char_p
@@ -232,7 +234,7 @@ class Lattice:
         return self.lbm_ace_steps_done()
 
     def lbm_ace_launch_shape(self):
-        v = [ctypes.c_int() for _ in range(4)]
+        v = [ctypes.c_int() for _ in range(5)]
         _check(self.ctx, self._lib.lbm_ace_launch_shape(self.ctx, *[ctypes.byref(x) for x in v]))
         return tuple(x.value for x in v)
 

@@ -34,7 +34,7 @@ VEL = {"vortex": (O.VORTEX, A.VEL_SINGLE_VORTEX), "uniform": (O.UNIFORM, A.VEL_U
 
 
 def pair(nx, ny, *, tau=0.8, eps=1.0, model=0, vel="vortex", T=100.0, U0=0.05, sign=-1.0,
-         ux=0.02, uy=-0.015, precision=A.F64, rows=0, phi0=None, seed=0):
+         ux=0.02, uy=-0.015, precision=A.F64, rows=0, phi0=None, seed=0, variant=0):
     """Matching oracle parameters and library keyword arguments."""
     ok, ak = VEL[vel]
     uf = vf = None
@@ -45,7 +45,8 @@ def pair(nx, ny, *, tau=0.8, eps=1.0, model=0, vel="vortex", T=100.0, U0=0.05, s
     op = O.Params(nx=nx, ny=ny, tau=tau, eps=eps, model=model, vel_kind=ok, U0=U0, T=T, sign=sign,
                   ux=ux, uy=uy, ufield=uf, vfield=vf)
     kw = dict(nx=nx, ny=ny, tau=tau, eps=eps, model=model, velocity_kind=ak, U0=U0, T_period=T,
-              vortex_sign=sign, ux=ux, uy=uy, precision=precision, rows_per_cta=rows)
+              vortex_sign=sign, ux=ux, uy=uy, precision=precision, rows_per_cta=rows,
+              kernel_variant=variant)
     if uf is not None:
         kw["u_field"], kw["v_field"] = uf, vf
     if phi0 is not None:
@@ -67,13 +68,24 @@ def rel_max(a, b):
     return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
 
 
-SHAPES = [(8, 8), (16, 16), (64, 64), (9, 7), (37, 53), (130, 20), (257, 70), (3, 3), (3, 5)]
+SHAPES = [(8, 8), (16, 16), (64, 64), (9, 7), (37, 53), (130, 20), (257, 70), (3, 3), (3, 5),
+          (4, 9), (132, 40), (260, 33)]
 
 
-@pytest.mark.parametrize("nx,ny", SHAPES)
+def variants(nx, precision):
+    """Kernel variants valid for this width: direct loads always, the bulk-copy pipeline
+    when a row is a multiple of 16 bytes."""
+    elem = 8 if precision == A.F64 else 4
+    return [A.KERNEL_DIRECT] + ([A.KERNEL_BULK] if (nx * elem) % 16 == 0 else [])
+
+
+CASES = [(nx, ny, v) for nx, ny in SHAPES for v in variants(nx, A.F64)]
+
+
+@pytest.mark.parametrize("nx,ny,variant", CASES)
 @pytest.mark.parametrize("model", [A.MODEL_MODIFIED, A.MODEL_CONSERVATIVE])
-def test_f64_one_step_matches_oracle(nx, ny, model):
-    op, kw = pair(nx, ny, model=model)
+def test_f64_one_step_matches_oracle(nx, ny, variant, model):
+    op, kw = pair(nx, ny, model=model, variant=variant)
     s = oracle_state(op, seed=nx * 1000 + ny)
     with A.Lattice(**kw) as g:
         g.set_state(s.f, s.phi_prev, s.t)
@@ -104,11 +116,13 @@ def test_f64_velocity_sources_and_first_step(vel, t0):
 
 
 @pytest.mark.parametrize("rows", [1, 2, 3, 7, 64])
-def test_f64_launch_shapes_agree(rows):
-    """Rows per CTA changes only the tiling: one step matches the oracle, and ten steps
-    are bit-for-bit those of the default launch shape (the halo recomputation sums
-    the populations in the same order as the interior)."""
-    op, kw = pair(150, 53, rows=rows)
+@pytest.mark.parametrize("variant", [A.KERNEL_DIRECT, A.KERNEL_BULK])
+def test_f64_launch_shapes_agree(rows, variant):
+    """Rows per CTA and the kernel variant change only the tiling and how rows reach
+    the SM: one step matches the oracle, and ten steps are bit-for-bit those of the
+    default launch (the halo recomputation sums the populations in the same order as
+    the interior, and both variants share the collision code)."""
+    op, kw = pair(150, 53, rows=rows, variant=variant)
     s = oracle_state(op, seed=11)
     with A.Lattice(**kw) as g:
         assert g.launch_shape()[1] == min(rows, 53)  # clamped to ny
@@ -117,7 +131,7 @@ def test_f64_launch_shapes_agree(rows):
         f, _ = g.get_state()
         g.step(9)
         f10, pp10 = g.get_state()
-    with A.Lattice(**{**kw, "rows_per_cta": 0}) as d:
+    with A.Lattice(**{**kw, "rows_per_cta": 0, "kernel_variant": A.KERNEL_DIRECT}) as d:
         d.set_state(s.f, s.phi_prev, s.t)
         d.step(10)
         fd, ppd = d.get_state()
@@ -162,9 +176,10 @@ def test_f64_full_vortex_period_64():
     assert e1g == pytest.approx(e1o, rel=1e-7)
 
 
-@pytest.mark.parametrize("nx,ny", [(64, 64), (37, 53), (257, 70)])
-def test_f32_one_step_close_to_oracle(nx, ny):
-    op, kw = pair(nx, ny, precision=A.F32)
+@pytest.mark.parametrize("nx,ny,variant", [(nx, ny, v) for nx, ny in [(64, 64), (37, 53), (257, 70), (260, 33)]
+                                            for v in variants(nx, A.F32)])
+def test_f32_one_step_close_to_oracle(nx, ny, variant):
+    op, kw = pair(nx, ny, precision=A.F32, variant=variant)
     s = oracle_state(op, seed=3)
     with A.Lattice(**kw) as g:
         g.set_state(s.f, s.phi_prev, s.t)
@@ -195,6 +210,7 @@ def test_f32_full_period_256_phi_l2():
 
 @pytest.mark.parametrize("precision,tol", [(A.F32, 2e-6), (A.F64, ONE_STEP)])
 def test_full_size_2048_sampled_nodes(precision, tol):
+    # default launch: the kernel variant and shape the benchmark uses
     """The 2048^2 lattice in the benchmark's launch shape: one step from an oracle-made
     state, checked at 512 sampled nodes (plus the four corners and the tile seams)
     against the oracle's per-node evaluation, and exact global mass bookkeeping."""
@@ -297,3 +313,17 @@ def test_callback_time_dependent_matches_oracle_vortex():
     with A.Lattice(nx=L, ny=L, vel_fn=vortex, phi0=phi0) as g:
         g.step(30)
         assert rel_max(g.phi(), s.phi()) <= MULTI_STEP
+
+
+@pytest.mark.parametrize("L,precision", [(2048, A.F32), (512, A.F64), (260, A.F32), (132, A.F64)])
+def test_kernel_variants_are_bit_identical(L, precision):
+    """The bulk-copy pipeline and the direct-load kernel do the same arithmetic on the
+    same values: 12 steps of the single vortex agree bit for bit."""
+    v = W.vortex_fp32(L)
+    out = []
+    for variant in (A.KERNEL_DIRECT, A.KERNEL_BULK):
+        with A.vortex_lattice(L, precision=precision, kernel_variant=variant) as g:
+            assert g.launch_shape()[4] == variant
+            g.step(12)
+            out.append(g.get_state())
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
