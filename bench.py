@@ -32,6 +32,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "MLUPS"
+KERNEL_NAME = {1: "ace_step", 2: "ace_step_bulk", 3: "ace_step_warp", 4: "ace_step_pair"}
 BYTES_PER_LUP = {"f64": 160, "f32": 80}
 L2_NOTE = "inputs larger than L2: 2 x 151 MB FP32 population buffers + 16.8 MB phi plane"
 
@@ -45,7 +46,7 @@ def parse():
     ap.add_argument("--L", type=int, default=2048)
     ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
     ap.add_argument("--rows", type=int, default=0, help="rows per CTA (0: library default)")
-    ap.add_argument("--variant", type=int, default=0, help="step kernel: 0 auto, 1 direct loads, 2 bulk-copy pipeline")
+    ap.add_argument("--variant", type=int, default=0, help="step kernel: 0 auto, 1 direct loads, 2 bulk-copy pipeline, 3 independent warps, 4 column pairs")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -139,7 +140,7 @@ def rejected(clk):
 def kernel_source_hash() -> str:
     """Hash of the step kernels' device sources (both variants)."""
     h = hashlib.sha256()
-    for name in ("ace_kernels.cuh", "ace_step_bulk.cuh"):
+    for name in ("ace_kernels.cuh", "ace_step_bulk.cuh", "ace_step_warp.cuh", "ace_step_pair.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2203_05230_gb300", "csrc", name), "rb").read())
     return h.hexdigest()[:16]
 
@@ -277,7 +278,7 @@ def run_ours(args):
     bpl = BYTES_PER_LUP[args.precision] * args.L * args.L
     peak, peak_kind = measured_peak()
     achieved = bpl / per_launch / 1e9
-    traffic = stored_traffic("ace_step_bulk" if shape[4] == 2 else "ace_step", args.precision, args.L)
+    traffic = stored_traffic(KERNEL_NAME[shape[4]], args.precision, args.L)
     lat.close()
 
     e2e = None
@@ -290,14 +291,16 @@ def run_ours(args):
             "config": {**cfg, "launch": {"tile_x": shape[0], "rows_per_cta": shape[1],
                                          "grid": [shape[2], shape[3]],
                                          "kernel": {1: "ace_step (direct loads)",
-                                                    2: "ace_step_bulk (bulk-copy pipeline)"}[shape[4]]},
+                                                    2: "ace_step_bulk (bulk-copy pipeline)",
+                                                    3: "ace_step_warp (independent warps)",
+                                                    4: "ace_step_pair (two columns per thread)"}[shape[4]]},
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                          else "fallback",
                          "algorithmic_bytes_per_launch": bpl,
-                         "kernel": "lbmace::ace_step_bulk" if shape[4] == 2 else "lbmace::ace_step"},
+                         "kernel": "lbmace::" + KERNEL_NAME[shape[4]]},
             "hbm_gbs_algorithmic": achieved,
             "mass_drift_rel_timed": (m1 - m0) / m0,
             "clocks": clk, "gpu_launches": args.steps, "e2e": e2e}

@@ -116,10 +116,12 @@ typedef struct lbm_ace_params {
     void* stream;        /* cudaStream_t for all device work; NULL = the legacy default stream */
     int rows_per_cta;    /* launch shape of the fused step: rows each CTA marches over;
                             0 selects a default for the lattice size and the device */
-    int kernel_variant;  /* fused step kernel: 0 = automatic, 1 = direct global loads,
-                            2 = rows staged in shared memory by bulk copies (needs
-                            nx * element size a multiple of 16 bytes). Both give
-                            bit-identical results. */
+    int kernel_variant;  /* fused step kernel: 0 = automatic (4 for even nx, else 1), 1 = direct global
+                            loads with a CTA-wide row barrier, 2 = rows staged in shared
+                            memory by bulk copies (needs nx * element size a multiple of
+                            16 bytes), 3 = independent 32-column warps with loads issued a
+                            row ahead, 4 = two columns per thread with paired loads and
+                            stores (needs an even nx). All give bit-identical results. */
 } lbm_ace_params;
 
 typedef struct lbm_ace_ctx lbm_ace_ctx; /* opaque; owns its device buffers */
@@ -166,7 +168,7 @@ int lbm_ace_set_state(lbm_ace_ctx* c, const double* f, const double* phi_prev, l
 long long lbm_ace_steps_done(const lbm_ace_ctx* c);
 
 /* Launch shape chosen for the fused step: columns and rows per CTA, grid, and the
- * kernel variant (1 or 2, see lbm_ace_params.kernel_variant). Any pointer may be NULL. */
+ * kernel variant (1 to 4, see lbm_ace_params.kernel_variant). Any pointer may be NULL. */
 int lbm_ace_launch_shape(const lbm_ace_ctx* c, int* tile_x, int* rows_per_cta, int* grid_x, int* grid_y,
                          int* kernel_variant);
 

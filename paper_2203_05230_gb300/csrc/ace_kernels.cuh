@@ -81,17 +81,21 @@ struct StepArgs {
     T delta, inv1p2d;          // regulariser d, 1/(1 + 2 d)
 };
 
-// Prescribed velocities. `col` caches what depends on x only; `at` gives u(t), u(t-1).
+// Prescribed velocities. `col(x)` holds what depends on x only, `rowv(col, x, y)` what
+// else a thread needs for node (x, y) (so it can be requested ahead of use), and
+// `at(col, row, ...)` gives u(t) and u(t-1) from the two.
 template <typename T>
 struct VelVortex { // Eq. 14: u = A sx2[x] s2y[y] c(t), v = -A sy2[y] s2x[x] c(t)
     const T* sx2; const T* s2x; const T* sy2; const T* s2y;
     T amp, ct, ctm1;
     struct Col { T sx2, s2x; };
+    struct Row { T sy2, s2y; };
     __device__ __forceinline__ Col col(int x) const { return {sx2[x], s2x[x]}; }
-    __device__ __forceinline__ void at(const Col& c, int x, int y, T& u, T& v, T& up, T& vp) const
+    __device__ __forceinline__ Row rowv(const Col&, int, int y) const { return {sy2[y], s2y[y]}; }
+    __device__ __forceinline__ void at(const Col& c, const Row& r, T& u, T& v, T& up, T& vp) const
     {
-        const T us = amp * c.sx2 * s2y[y];
-        const T vs = -amp * sy2[y] * c.s2x;
+        const T us = amp * c.sx2 * r.s2y;
+        const T vs = -amp * r.sy2 * c.s2x;
         u = us * ct; v = vs * ct; up = us * ctm1; vp = vs * ctm1;
     }
 };
@@ -100,8 +104,10 @@ template <typename T>
 struct VelUniform {
     T ux, uy;
     struct Col {};
+    struct Row {};
     __device__ __forceinline__ Col col(int) const { return {}; }
-    __device__ __forceinline__ void at(const Col&, int, int, T& u, T& v, T& up, T& vp) const
+    __device__ __forceinline__ Row rowv(const Col&, int, int) const { return {}; }
+    __device__ __forceinline__ void at(const Col&, const Row&, T& u, T& v, T& up, T& vp) const
     {
         u = ux; v = uy; up = ux; vp = uy;
     }
@@ -112,11 +118,16 @@ struct VelPlanes { // device FP64 planes of u(t), v(t), u(t-1), v(t-1)
     const double* u; const double* v; const double* up; const double* vp;
     int nx;
     struct Col {};
+    struct Row { T u, v, up, vp; };
     __device__ __forceinline__ Col col(int) const { return {}; }
-    __device__ __forceinline__ void at(const Col&, int x, int y, T& uu, T& vv, T& upp, T& vpp) const
+    __device__ __forceinline__ Row rowv(const Col&, int x, int y) const
     {
         const long long k = (long long)y * nx + x;
-        uu = T(u[k]); vv = T(v[k]); upp = T(up[k]); vpp = T(vp[k]);
+        return {T(u[k]), T(v[k]), T(up[k]), T(vp[k])};
+    }
+    __device__ __forceinline__ void at(const Col&, const Row& r, T& uu, T& vv, T& upp, T& vpp) const
+    {
+        uu = r.u; vv = r.v; upp = r.up; vpp = r.vp;
     }
 };
 
@@ -174,12 +185,14 @@ __device__ __forceinline__ T chi_of(T ph, const StepArgs<T>& a)
 
 // Steps a4-a12 for one node (x, yc): gradient of chi from the three stencil rows
 // (cS/cC/cN point at column x - 1 of rows yc - 1, yc, yc + 1), normal, sharpening,
-// velocity, time derivative, forcing, equilibrium, BGK, and the 9 stores of f*.
+// velocity, time derivative, forcing, equilibrium, BGK, and the 9 stores of f* (or,
+// when `out` is given, the 9 values of f* written there for the caller to store).
 // f: pulled populations f_i(x, t); ph = phi(x, t); pp = phi(x, t - 1).
 template <typename T, int MODEL, class Vel>
-__device__ __forceinline__ void collide_node(const StepArgs<T>& a, const Vel& vel, const typename Vel::Col& vcol,
-                                             int x, int yc, const T* f, T ph, T pp,
-                                             const T* cS, const T* cC, const T* cN)
+__device__ __forceinline__ void collide_node_row(const StepArgs<T>& a, const Vel& vel, const typename Vel::Col& vcol,
+                                                 const typename Vel::Row& vrow, int x, int yc, const T* f, T ph,
+                                                 T pp, const T* cS, const T* cC, const T* cN, bool store = true,
+                                                 T* out = nullptr)
 {
     const T third = T(1) / T(3), twelfth = T(1) / T(12);
     // 3 sum_i w_i c_i chi(x + c_i): axis neighbours weigh 3/9, diagonals 3/36
@@ -196,7 +209,7 @@ __device__ __forceinline__ void collide_node(const StepArgs<T>& a, const Vel& ve
         S = ph * (T(1) - ph) * a.inv_eps;
     }
     T u, v, up, vp;
-    vel.at(vcol, x, yc, u, v, up, vp);
+    vel.at(vcol, vrow, u, v, up, vp);
     T dx = T(0), dy = T(0);
     if (!a.first) {
         dx = ph * u - pp * up;
@@ -227,31 +240,56 @@ __device__ __forceinline__ void collide_node(const StepArgs<T>& a, const Vel& ve
 #pragma unroll
     for (int i = 1; i < 9; ++i) rest += fs[i];
     fs[0] = ph - rest;
-    T* o = a.fout + (long long)yc * a.nx + x;
+    if (out) {
 #pragma unroll
-    for (int i = 0; i < 9; ++i) o[(long long)i * a.plane] = fs[i];
+        for (int i = 0; i < 9; ++i) out[i] = fs[i];
+    } else if (store) {
+        // 32-bit element offsets (9 nx ny < 2^31 is checked on the host); the plane
+        // offsets i * plane are the same for the whole warp
+        const unsigned o = (unsigned)yc * (unsigned)a.nx + (unsigned)x;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) a.fout[o + (unsigned)i * (unsigned)a.plane] = fs[i];
+    }
+}
+
+template <typename T, int MODEL, class Vel>
+__device__ __forceinline__ void collide_node(const StepArgs<T>& a, const Vel& vel, const typename Vel::Col& vcol,
+                                             int x, int yc, const T* f, T ph, T pp,
+                                             const T* cS, const T* cC, const T* cN, bool store = true)
+{
+    collide_node_row<T, MODEL>(a, vel, vcol, vel.rowv(vcol, x, yc), x, yc, f, ph, pp, cS, cC, cN, store);
 }
 
 // Population i of node (x, y) at time t, pulled from f*(t-1) at (x - c_i, y - c_i).
-// xm/xp/rm/rp are the wrapped neighbour column/row indices.
+// ro_m/ro_0/ro_p are the element offsets of rows r-1, r, r+1 (wrapped, times nx) and
+// xm/x/xp the wrapped columns; 32-bit offsets with warp-uniform plane strides.
+template <typename T>
+__device__ __forceinline__ void pull_row(const T* __restrict__ fin, unsigned plane, unsigned ro_m, unsigned ro_0,
+                                         unsigned ro_p, unsigned xm, unsigned x, unsigned xp, T* f)
+{
+    f[0] = fin[ro_0 + x];
+    f[1] = fin[plane + ro_0 + xm];
+    f[2] = fin[2u * plane + ro_m + x];
+    f[3] = fin[3u * plane + ro_0 + xp];
+    f[4] = fin[4u * plane + ro_p + x];
+    f[5] = fin[5u * plane + ro_m + xm];
+    f[6] = fin[6u * plane + ro_m + xp];
+    f[7] = fin[7u * plane + ro_p + xp];
+    f[8] = fin[8u * plane + ro_p + xm];
+}
+
+// The same with row indices (used by the variants that index rows directly).
 template <typename T>
 __device__ __forceinline__ void pull_row(const T* __restrict__ fin, long long plane, int nx,
                                          int r, int rm, int rp, int x, int xm, int xp, T* f)
 {
-    const T* p = fin;
-    f[0] = p[(long long)r * nx + x];   p += plane;
-    f[1] = p[(long long)r * nx + xm];  p += plane;
-    f[2] = p[(long long)rm * nx + x];  p += plane;
-    f[3] = p[(long long)r * nx + xp];  p += plane;
-    f[4] = p[(long long)rp * nx + x];  p += plane;
-    f[5] = p[(long long)rm * nx + xm]; p += plane;
-    f[6] = p[(long long)rm * nx + xp]; p += plane;
-    f[7] = p[(long long)rp * nx + xp]; p += plane;
-    f[8] = p[(long long)rp * nx + xm];
+    const unsigned n = (unsigned)nx;
+    pull_row(fin, (unsigned)plane, (unsigned)rm * n, (unsigned)r * n, (unsigned)rp * n, (unsigned)xm, (unsigned)x,
+             (unsigned)xp, f);
 }
 
 template <typename T, int MODEL, class Vel>
-__global__ void __launch_bounds__(TILE_X) ace_step(const StepArgs<T> a, const Vel vel)
+__global__ void __launch_bounds__(TILE_X, sizeof(T) == 4 ? 8 : 1) ace_step(const StepArgs<T> a, const Vel vel)
 {
     __shared__ T chi_s[4][TILE_X + 2];
     __shared__ double red_s[TILE_X / 32];
@@ -261,12 +299,14 @@ __global__ void __launch_bounds__(TILE_X) ace_step(const StepArgs<T> a, const Ve
     const int x0 = blockIdx.x * TILE_X;
     const int w = min(TILE_X, a.nx - x0);
     const bool act = tx < w;
-    const int x = x0 + (act ? tx : 0);
+    // threads beyond a ragged strip's width work on its last column and store nothing
+    const int x = x0 + (act ? tx : w - 1);
     const int xm = x == 0 ? a.nx - 1 : x - 1;
     const int xp = x == a.nx - 1 ? 0 : x + 1;
     const int y0 = blockIdx.y * a.rows;
     const int y1 = min(y0 + a.rows, a.ny);
     const int nk = y1 - y0 + 2; // rows y0-1 .. y1 get phi and chi
+    const unsigned nxu = (unsigned)a.nx, plane = (unsigned)a.plane;
 
     // Halo lanes of warp 0: lanes 0..8 pull population `hi` of the column left of
     // the strip, lanes 16..24 that of the column right of it.
@@ -278,26 +318,33 @@ __global__ void __launch_bounds__(TILE_X) ace_step(const StepArgs<T> a, const Ve
         hcol = wrap_idx(c - cx_of(hi), a.nx);
     }
     const int hcy = halo ? cy_of(hi) : 0;
-    const T* hplane = a.fin + (long long)(halo ? hi : 0) * a.plane;
+    const unsigned hbase = (unsigned)(halo ? hi : 0) * plane + (unsigned)hcol;
 
     const typename Vel::Col vcol = vel.col(x);
 
-    T fa[9], fb[9];
+    T ra[9], rb[9], rc[9]; // pulled row r, row r - 1, row r + 1 (prefetched)
     T hv = T(0);
     T phb = T(0);
     double msum = 0.0; // FP64 column sum of phi over this thread's rows
 
-    {
-        const int r = wrap_idx(y0 - 1, a.ny);
-        if (act) pull_row(a.fin, a.plane, a.nx, r, wrap_idx(r - 1, a.ny), wrap_idx(r + 1, a.ny), x, xm, xp, fa);
-        if (halo) hv = hplane[(long long)wrap_idx(r - hcy, a.ny) * a.nx + hcol];
-    }
+    // rows r - 1, r, r + 1 of the row being pulled, as element offsets
+    int r = wrap_idx(y0 - 1, a.ny);
+    auto load = [&](int rr, T (&dst)[9]) {
+        const int rm = rr == 0 ? a.ny - 1 : rr - 1, rp = rr == a.ny - 1 ? 0 : rr + 1;
+        pull_row(a.fin, plane, (unsigned)rm * nxu, (unsigned)rr * nxu, (unsigned)rp * nxu, (unsigned)xm,
+                 (unsigned)x, (unsigned)xp, dst);
+        if (halo) hv = a.fin[hbase + (unsigned)wrap_idx(rr - hcy, a.ny) * nxu];
+    };
+    load(r, ra);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) rb[i] = rc[i] = T(0);
 
+#pragma unroll 1
     for (int k = 0; k < nk; ++k) {
-        // Row r = y0 - 1 + k: phi (Eq. 12) and chi into the ring slot k & 3.
+        // row r = y0 - 1 + k: phi (Eq. 12) and chi into the ring slot k & 3
         T ph = T(0);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) ph += fa[i];
+        for (int i = 0; i < 9; ++i) ph += ra[i];
         if (act) chi_s[k & 3][1 + tx] = chi_of<T, MODEL>(ph, a);
         if (tx < 32) {
             const int base = lane & 16;
@@ -308,28 +355,23 @@ __global__ void __launch_bounds__(TILE_X) ace_step(const StepArgs<T> a, const Ve
             if (lane == 16) chi_s[k & 3][w + 1] = chi_of<T, MODEL>(hs, a);
         }
         __syncthreads();
-
-        T fc[9];
-#pragma unroll
-        for (int i = 0; i < 9; ++i) fc[i] = fa[i];
-        if (k + 1 < nk) { // prefetch row r + 1 while row r - 1 collides
-            const int r = wrap_idx(y0 + k, a.ny);
-            if (act) pull_row(a.fin, a.plane, a.nx, r, wrap_idx(r - 1, a.ny), wrap_idx(r + 1, a.ny), x, xm, xp, fa);
-            if (halo) hv = hplane[(long long)wrap_idx(r - hcy, a.ny) * a.nx + hcol];
-        }
-
-        if (k >= 2 && act) {
-            // Collide row yc = y0 + k - 2 with its pulled populations fb and phi phb.
+        r = r == a.ny - 1 ? 0 : r + 1;
+        if (k + 1 < nk) load(r, rc); // row r + 1 while row r - 1 collides
+        if (k >= 2) {
+            // collide row yc = y0 + k - 2 with its pulled populations rb and phi phb
             const int yc = y0 + k - 2;
-            T* phr = a.phi + (long long)yc * a.nx + x;
-            const T pp = a.first ? T(0) : *phr;
-            collide_node<T, MODEL>(a, vel, vcol, x, yc, fb, phb, pp, chi_s[(k - 2) & 3] + tx,
-                                   chi_s[(k - 1) & 3] + tx, chi_s[k & 3] + tx);
-            *phr = phb;
-            msum += (double)phb;
+            const unsigned po = (unsigned)yc * nxu + (unsigned)x;
+            const T pp = a.first ? T(0) : a.phi[po];
+            const int j = act ? tx : w - 1; // stencil column in the ring
+            collide_node<T, MODEL>(a, vel, vcol, x, yc, rb, phb, pp, chi_s[(k - 2) & 3] + j,
+                                   chi_s[(k - 1) & 3] + j, chi_s[k & 3] + j, act);
+            if (act) {
+                a.phi[po] = phb;
+                msum += (double)phb;
+            }
         }
 #pragma unroll
-        for (int i = 0; i < 9; ++i) fb[i] = fc[i];
+        for (int i = 0; i < 9; ++i) { rb[i] = ra[i]; ra[i] = rc[i]; }
         phb = ph;
     }
 
@@ -359,7 +401,8 @@ __global__ void ace_init(const double* __restrict__ phi0, T* __restrict__ fst, T
         const int x = (int)(k % nx), y = (int)(k / nx);
         const T ph = T(phi0[k]);
         T u, v, up, vp, feq[9];
-        vel.at(vel.col(x), x, y, u, v, up, vp);
+        const typename Vel::Col c = vel.col(x);
+        vel.at(c, vel.rowv(c, x, y), u, v, up, vp);
         equilibrium(ph, u, v, feq);
 #pragma unroll
         for (int i = 0; i < 9; ++i)

@@ -131,29 +131,29 @@ __global__ void __launch_bounds__(TX) ace_step_bulk(const StepArgs<T> a, const V
     }
 
     const typename Vel::Col vcol = vel.col(x);
-    T fb[9];
+    T ra[9], rb[9]; // pulled row r, row r - 1
 #pragma unroll
-    for (int i = 0; i < 9; ++i) fb[i] = T(0);
+    for (int i = 0; i < 9; ++i) ra[i] = rb[i] = T(0);
     T phb = T(0);
-    double msum = 0.0; // FP64 column sum of phi over this thread's rows
+    double msum = 0.0;    // FP64 column sum of phi over this thread's rows
     bool ok = true;       // this thread's waits all completed
     bool aborted = false; // some thread's wait gave up (uniform across the CTA)
     int waited = 0;       // source indices this thread has seen complete
 
-    for (int k = 0; k < nk; ++k) {
-        // sources k, k+1, k+2 (rows r-1, r, r+1 of pulled row r = y0-1+k) must be in
+    // Pulled row r = y0 - 1 + k into `cur`; row r - 1 (in `prev`) collides once psi of
+    // rows r - 2 .. r is in the ring. Returns false when the CTA gives up.
+    auto row = [&](int k, T (&cur)[9], const T (&prev)[9]) -> bool {
+        // sources k, k+1, k+2 (rows r-1, r, r+1) must be in
         for (; waited <= k + 2; ++waited)
             if (ok && !mbar_wait_bounded(&sm.bar[waited % STAGES], (uint32_t)((waited / STAGES) & 1), kWaitLimitCycles))
                 ok = false;
-
-        T fa[9];
         T ph = T(0);
         if (act) {
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
                 const int q = k + 1 - cy_of(i);
-                fa[i] = sm.f[q % STAGES][i][tx + H - cx_of(i)];
-                ph += fa[i];
+                cur[i] = sm.f[q % STAGES][i][tx + H - cx_of(i)];
+                ph += cur[i];
             }
             sm.chi[k & 3][1 + tx] = chi_of<T, MODEL>(ph, a);
         }
@@ -168,10 +168,7 @@ __global__ void __launch_bounds__(TX) ace_step_bulk(const StepArgs<T> a, const V
                 sm.chi[k & 3][side == 0 ? 0 : w + 1] = chi_of<T, MODEL>(hs, a);
             }
         }
-        if (__syncthreads_or(!ok)) { // a barrier whose result every thread shares
-            aborted = true;
-            break;
-        }
+        if (__syncthreads_or(!ok)) return false; // a barrier whose result every thread shares
 
         // refill the stage freed by source index k - 1 (consumed by all threads)
         if (tx == 0 && k >= 1 && issued < nsrc) {
@@ -179,18 +176,22 @@ __global__ void __launch_bounds__(TX) ace_step_bulk(const StepArgs<T> a, const V
             issue(issued);
             ++issued;
         }
-
         if (k >= 2 && act) {
             const int yc = y0 + k - 2; // source index k
             const T pp = sm.phi[k % STAGES][tx];
-            collide_node<T, MODEL>(a, vel, vcol, x, yc, fb, phb, pp, sm.chi[(k - 2) & 3] + tx,
+            collide_node<T, MODEL>(a, vel, vcol, x, yc, prev, phb, pp, sm.chi[(k - 2) & 3] + tx,
                                    sm.chi[(k - 1) & 3] + tx, sm.chi[k & 3] + tx);
             a.phi[(long long)yc * a.nx + x] = phb;
             msum += (double)phb;
         }
-#pragma unroll
-        for (int i = 0; i < 9; ++i) fb[i] = fa[i];
         phb = ph;
+        return true;
+    };
+#pragma unroll 1
+    for (int k = 0; k < nk; ++k) {
+        if (!row(k, ra, rb)) { aborted = true; break; }
+#pragma unroll
+        for (int i = 0; i < 9; ++i) rb[i] = ra[i];
     }
 
     if (aborted) {

@@ -6,6 +6,8 @@
 #include "lbm_ace.h"
 #include "ace_kernels.cuh"
 #include "ace_step_bulk.cuh"
+#include "ace_step_warp.cuh"
+#include "ace_step_pair.cuh"
 
 #include <cuda_runtime.h>
 
@@ -149,6 +151,10 @@ void launch_step_k(lbm_ace_ctx* c, const Vel& vel)
     if (c->variant == 2)
         ace_step_bulk<T, MODEL, Vel, BULK_TX, BULK_STAGES>
             <<<grid, BULK_TX, c->smem, c->stream>>>(make_args<T>(c), vel, c->dev_err);
+    else if (c->variant == 3)
+        ace_step_warp<T, MODEL, Vel><<<grid, TILE_X, 0, c->stream>>>(make_args<T>(c), vel);
+    else if (c->variant == 4)
+        ace_step_pair<T, MODEL, Vel><<<grid, PAIR_THREADS, 0, c->stream>>>(make_args<T>(c), vel);
     else
         ace_step<T, MODEL, Vel><<<grid, TILE_X, 0, c->stream>>>(make_args<T>(c), vel);
 }
@@ -233,6 +239,14 @@ int occupancy_k(lbm_ace_ctx* c, int* blocks)
         c->tile_x = BULK_TX;
         CK(c, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem));
         CK(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k, BULK_TX, c->smem));
+    } else if (c->variant == 3) {
+        c->smem = 0;
+        c->tile_x = TILE_X;
+        CK(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, ace_step_warp<T, MODEL, Vel>, TILE_X, 0));
+    } else if (c->variant == 4) {
+        c->smem = 0;
+        c->tile_x = PAIR_COLS;
+        CK(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, ace_step_pair<T, MODEL, Vel>, PAIR_THREADS, 0));
     } else {
         c->smem = 0;
         c->tile_x = TILE_X;
@@ -387,8 +401,9 @@ static int init_impl(lbm_ace_ctx* c, const lbm_ace_params* p)
     CK(c, cudaMemset(c->dev_err, 0, sizeof(int)));
 
     // kernel variant: the bulk-copy pipeline needs 16-byte aligned rows
-    const bool bulk_ok = ((size_t)nx * c->elem) % 16 == 0;
-    c->variant = p->kernel_variant == 0 ? (bulk_ok ? 2 : 1) : p->kernel_variant;
+    // automatic choice: column pairs when nx is even (fastest measured on GB300 at
+    // 2048^2), else direct loads
+    c->variant = p->kernel_variant != 0 ? p->kernel_variant : (nx % 2 == 0 ? 4 : 1);
 
     // launch shape of the fused step: one wave of resident CTAs when possible
     int occ = 0;
@@ -503,8 +518,10 @@ int lbm_ace_init(const lbm_ace_params* p, lbm_ace_ctx** out)
         return fail(nullptr, LBM_ACE_EINVAL, "disk centre/radius not finite");
     }
     if (p->rows_per_cta < 0) return fail(nullptr, LBM_ACE_EINVAL, "rows_per_cta must be >= 0");
-    if (p->kernel_variant < 0 || p->kernel_variant > 2)
+    if (p->kernel_variant < 0 || p->kernel_variant > 4)
         return fail(nullptr, LBM_ACE_EINVAL, "kernel_variant %d unknown", p->kernel_variant);
+    if (p->kernel_variant == 4 && p->nx % 2 != 0)
+        return fail(nullptr, LBM_ACE_EINVAL, "kernel_variant 4 needs an even nx (nx = %d)", p->nx);
     if (p->kernel_variant == 2) {
         const size_t elem = p->precision == LBM_ACE_F64 ? 8 : 4;
         if (((size_t)p->nx * elem) % 16 != 0)

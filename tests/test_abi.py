@@ -77,7 +77,8 @@ def test_defaults_are_the_64x64_vortex():
     (dict(T_period=0.0), "T_period"),
     (dict(velocity_kind=A.VEL_FIELD), "velocity field"),
     (dict(rows_per_cta=-1), "rows_per_cta"),
-    (dict(kernel_variant=3), "kernel_variant"),
+    (dict(kernel_variant=5), "kernel_variant"),
+    (dict(nx=65, kernel_variant=4), "even nx"),
     (dict(nx=66, precision=1, kernel_variant=2), "multiple of 16"),
     (dict(nx=67, precision=0, kernel_variant=2), "multiple of 16"),
 ])

@@ -69,14 +69,15 @@ def rel_max(a, b):
 
 
 SHAPES = [(8, 8), (16, 16), (64, 64), (9, 7), (37, 53), (130, 20), (257, 70), (3, 3), (3, 5),
-          (4, 9), (132, 40), (260, 33)]
+          (4, 9), (132, 40), (260, 33), (258, 11), (514, 21)]
 
 
 def variants(nx, precision):
-    """Kernel variants valid for this width: direct loads always, the bulk-copy pipeline
-    when a row is a multiple of 16 bytes."""
+    """Kernel variants valid for this width: direct loads and independent warps always,
+    the bulk-copy pipeline when a row is a multiple of 16 bytes."""
     elem = 8 if precision == A.F64 else 4
-    return [A.KERNEL_DIRECT] + ([A.KERNEL_BULK] if (nx * elem) % 16 == 0 else [])
+    return ([A.KERNEL_DIRECT, A.KERNEL_WARP] + ([A.KERNEL_BULK] if (nx * elem) % 16 == 0 else [])
+            + ([A.KERNEL_PAIR] if nx % 2 == 0 else []))
 
 
 CASES = [(nx, ny, v) for nx, ny in SHAPES for v in variants(nx, A.F64)]
@@ -116,7 +117,7 @@ def test_f64_velocity_sources_and_first_step(vel, t0):
 
 
 @pytest.mark.parametrize("rows", [1, 2, 3, 7, 64])
-@pytest.mark.parametrize("variant", [A.KERNEL_DIRECT, A.KERNEL_BULK])
+@pytest.mark.parametrize("variant", [A.KERNEL_DIRECT, A.KERNEL_BULK, A.KERNEL_WARP, A.KERNEL_PAIR])
 def test_f64_launch_shapes_agree(rows, variant):
     """Rows per CTA and the kernel variant change only the tiling and how rows reach
     the SM: one step matches the oracle, and ten steps are bit-for-bit those of the
@@ -317,13 +318,13 @@ def test_callback_time_dependent_matches_oracle_vortex():
 
 @pytest.mark.parametrize("L,precision", [(2048, A.F32), (512, A.F64), (260, A.F32), (132, A.F64)])
 def test_kernel_variants_are_bit_identical(L, precision):
-    """The bulk-copy pipeline and the direct-load kernel do the same arithmetic on the
-    same values: 12 steps of the single vortex agree bit for bit."""
-    v = W.vortex_fp32(L)
+    """The three kernel variants do the same arithmetic on the same values: 12 steps of
+    the single vortex agree bit for bit."""
     out = []
-    for variant in (A.KERNEL_DIRECT, A.KERNEL_BULK):
+    for variant in (A.KERNEL_DIRECT, A.KERNEL_BULK, A.KERNEL_WARP, A.KERNEL_PAIR):
         with A.vortex_lattice(L, precision=precision, kernel_variant=variant) as g:
             assert g.launch_shape()[4] == variant
             g.step(12)
             out.append(g.get_state())
-    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    for o in out[1:]:
+        assert np.array_equal(out[0][0], o[0]) and np.array_equal(out[0][1], o[1])
