@@ -32,8 +32,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "MLUPS"
-KERNEL_NAME = {1: "ace_step", 2: "ace_step_bulk", 3: "ace_step_warp", 4: "ace_step_pair"}
-BYTES_PER_LUP = {"f64": 160, "f32": 80}
+KERNEL_NAME = {1: "ace_step", 2: "ace_step_bulk", 3: "ace_step_warp", 4: "ace_step_pair", 5: "ace_step_dev"}
+BYTES_PER_LUP = {"f64": 160, "f32": 80, "f16dev": 44, "bf16dev": 44}
 L2_NOTE = "inputs larger than L2: 2 x 151 MB FP32 population buffers + 16.8 MB phi plane"
 
 
@@ -44,7 +44,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--L", type=int, default=2048)
-    ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--precision", default="f32", choices=["f32", "f64", "f16dev", "bf16dev"])
     ap.add_argument("--rows", type=int, default=0, help="rows per CTA (0: library default)")
     ap.add_argument("--variant", type=int, default=0, help="step kernel: 0 auto, 1 direct loads, 2 bulk-copy pipeline, 3 independent warps, 4 column pairs")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -60,7 +60,8 @@ def workload(args):
         "workload": f"single vortex {args.L}x{args.L} {args.precision.upper()} eps {v.eps} tau {v.tau} "
                     f"U0 {v.U0} T {v.T} steps, disk R {v.R:g} at ({v.xc:g}, {v.yc:g})",
         "lattice": [args.L, args.L], "T_period": v.T, "eps": v.eps, "tau": v.tau, "U0": v.U0,
-        "l2": L2_NOTE,
+        "l2": L2_NOTE if args.precision in ("f32", "f64") else
+              "inputs larger than L2: 2 x 75.5 MB 16-bit deviation buffers + 2 x 16.8 MB phi planes",
     }
 
 
@@ -140,7 +141,8 @@ def rejected(clk):
 def kernel_source_hash() -> str:
     """Hash of the step kernels' device sources (both variants)."""
     h = hashlib.sha256()
-    for name in ("ace_kernels.cuh", "ace_step_bulk.cuh", "ace_step_warp.cuh", "ace_step_pair.cuh"):
+    for name in ("ace_kernels.cuh", "ace_step_bulk.cuh", "ace_step_warp.cuh", "ace_step_pair.cuh",
+                 "ace_step_dev.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2203_05230_gb300", "csrc", name), "rb").read())
     return h.hexdigest()[:16]
 
@@ -233,7 +235,7 @@ def run_ours(args):
     dev = torch.cuda.current_device()
     from paper_2203_05230_gb300 import lbm_ace as A
     v, cfg = workload(args)
-    prec = {"f32": A.F32, "f64": A.F64}[args.precision]
+    prec = {"f32": A.F32, "f64": A.F64, "f16dev": A.F16DEV, "bf16dev": A.BF16DEV}[args.precision]
     stream = torch.cuda.current_stream()
     lat = A.vortex_lattice(args.L, eps=v.eps, tau=v.tau, U0=v.U0, T=v.T, precision=prec,
                            stream=stream.cuda_stream, device=dev, rows_per_cta=args.rows,
@@ -293,7 +295,8 @@ def run_ours(args):
                                          "kernel": {1: "ace_step (direct loads)",
                                                     2: "ace_step_bulk (bulk-copy pipeline)",
                                                     3: "ace_step_warp (independent warps)",
-                                                    4: "ace_step_pair (two columns per thread)"}[shape[4]]},
+                                                    4: "ace_step_pair (two columns per thread)",
+                                                    5: "ace_step_dev (16-bit deviations)"}[shape[4]]},
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,

@@ -65,7 +65,10 @@ enum {
 enum {
     LBM_ACE_F64 = 0,    /* FP64 populations, FP64 arithmetic */
     LBM_ACE_F32 = 1,    /* FP32 populations, FP32 arithmetic, FP64 mass sums */
-    LBM_ACE_F16DEV = 2, /* populations stored as FP16 deviations f_i - w_i phi, FP32 arithmetic */
+    LBM_ACE_F16DEV = 2, /* populations stored as FP16 deviations g_i = f*_i - s_i phi from split
+                           weights s = (1820, 455 x4, 114 x4)/4096 (close to the D2Q9
+                           weights, summing exactly to 1), phi in FP32, FP32 arithmetic,
+                           44 bytes per node update; needs an even nx */
     LBM_ACE_BF16DEV = 3 /* as above with BF16 storage */
 };
 
@@ -121,7 +124,9 @@ typedef struct lbm_ace_params {
                             memory by bulk copies (needs nx * element size a multiple of
                             16 bytes), 3 = independent 32-column warps with loads issued a
                             row ahead, 4 = two columns per thread with paired loads and
-                            stores (needs an even nx). All give bit-identical results. */
+                            stores (needs an even nx). All give bit-identical results.
+                            The 16-bit deviation storage has its own kernel (reported as 5)
+                            and takes 0 here. */
 } lbm_ace_params;
 
 typedef struct lbm_ace_ctx lbm_ace_ctx; /* opaque; owns its device buffers */
@@ -168,7 +173,7 @@ int lbm_ace_set_state(lbm_ace_ctx* c, const double* f, const double* phi_prev, l
 long long lbm_ace_steps_done(const lbm_ace_ctx* c);
 
 /* Launch shape chosen for the fused step: columns and rows per CTA, grid, and the
- * kernel variant (1 to 4, see lbm_ace_params.kernel_variant). Any pointer may be NULL. */
+ * kernel variant (1 to 5, see lbm_ace_params.kernel_variant). Any pointer may be NULL. */
 int lbm_ace_launch_shape(const lbm_ace_ctx* c, int* tile_x, int* rows_per_cta, int* grid_x, int* grid_y,
                          int* kernel_variant);
 

@@ -168,78 +168,137 @@ __device__ __forceinline__ float psi_clipped(float pc, float eps, float delta)
 __device__ __forceinline__ double inv_norm(double g2, double delta) { return 1.0 / (sqrt(g2) + delta); }
 __device__ __forceinline__ float inv_norm(float g2, float delta)
 {
-    const float g = g2 > 0.0f ? g2 * rsqrtf(g2) : 0.0f;
+    // |g| = g2 / sqrt(g2); below 1e-30 (far under delta) the floor only keeps 0 * inf away
+    const float g = g2 * rsqrtf(fmaxf(g2, 1e-30f));
     return __fdividef(1.0f, g + delta);
 }
+
+__device__ __forceinline__ float clip01(float v) { return fminf(fmaxf(v, 0.0f), 1.0f); }
+__device__ __forceinline__ double clip01(double v) { return fmin(fmax(v, 0.0), 1.0); }
 
 template <typename T, int MODEL>
 __device__ __forceinline__ T chi_of(T ph, const StepArgs<T>& a)
 {
     if (MODEL == MODEL_MODIFIED) {
-        const T pc = ph < T(0) ? T(0) : (ph > T(1) ? T(1) : ph);
-        return psi_clipped(pc, a.eps, a.delta);
+        return psi_clipped(clip01(ph), a.eps, a.delta);
     } else {
         return ph;
     }
 }
 
-// Steps a4-a12 for one node (x, yc): gradient of chi from the three stencil rows
-// (cS/cC/cN point at column x - 1 of rows yc - 1, yc, yc + 1), normal, sharpening,
-// velocity, time derivative, forcing, equilibrium, BGK, and the 9 stores of f* (or,
-// when `out` is given, the 9 values of f* written there for the caller to store).
-// f: pulled populations f_i(x, t); ph = phi(x, t); pp = phi(x, t - 1).
+template <typename T> struct Pair2;
+template <> struct Pair2<float> { using type = float2; };
+template <> struct Pair2<double> { using type = double2; };
+
+// Arithmetic with explicit rounding and no contraction left to the compiler, on one
+// node (float, double) or on two nodes at once (float2, the packed FP32x2 instructions
+// of sm_100 and later). Each float2 lane rounds exactly like the float operation, so
+// every kernel variant computes bit-identical populations.
+template <typename V> struct Ar;
+template <>
+struct Ar<float> {
+    using S = float;
+    __device__ __forceinline__ static float c(float s) { return s; }
+    __device__ __forceinline__ static float add(float a, float b) { return __fadd_rn(a, b); }
+    __device__ __forceinline__ static float sub(float a, float b) { return __fsub_rn(a, b); }
+    __device__ __forceinline__ static float mul(float a, float b) { return __fmul_rn(a, b); }
+    __device__ __forceinline__ static float fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+    __device__ __forceinline__ static float neg(float a) { return -a; }
+    template <class F> __device__ __forceinline__ static float map(float a, F f) { return f(a); }
+};
+template <>
+struct Ar<double> {
+    using S = double;
+    __device__ __forceinline__ static double c(double s) { return s; }
+    __device__ __forceinline__ static double add(double a, double b) { return __dadd_rn(a, b); }
+    __device__ __forceinline__ static double sub(double a, double b) { return __dsub_rn(a, b); }
+    __device__ __forceinline__ static double mul(double a, double b) { return __dmul_rn(a, b); }
+    __device__ __forceinline__ static double fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+    __device__ __forceinline__ static double neg(double a) { return -a; }
+    template <class F> __device__ __forceinline__ static double map(double a, F f) { return f(a); }
+};
+template <>
+struct Ar<float2> {
+    using S = float;
+    __device__ __forceinline__ static float2 c(float s) { return make_float2(s, s); }
+    __device__ __forceinline__ static float2 add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+    __device__ __forceinline__ static float2 neg(float2 a) { return make_float2(-a.x, -a.y); }
+    __device__ __forceinline__ static float2 sub(float2 a, float2 b) { return __fadd2_rn(a, neg(b)); }
+    __device__ __forceinline__ static float2 mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+    __device__ __forceinline__ static float2 fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+    template <class F> __device__ __forceinline__ static float2 map(float2 a, F f) { return make_float2(f(a.x), f(a.y)); }
+};
+
+// Steps a4-a11 on V (one node, or two nodes as float2): gradient of chi from the
+// stencil (cS*, cC*, cN*: rows yc - 1, yc, yc + 1; l/c/r: columns x - 1, x, x + 1),
+// normal, sharpening, time derivative, forcing, equilibrium and BGK. f: pulled
+// populations f_i(x, t); ph = phi(x, t); pp = phi(x, t - 1); u, v at t and up, vp at
+// t - 1. Writes the post-collision populations to fs.
+template <typename V, typename T, int MODEL>
+__device__ __forceinline__ void collide_core(const StepArgs<T>& a, const V* f, V ph, V pp, V cSl, V cSc, V cSr, V cCl,
+                                             V cCr, V cNl, V cNc, V cNr, V u, V v, V up, V vp, V* fs)
+{
+    using R = Ar<V>;
+    const V third = R::c(T(1) / T(3)), twelfth = R::c(T(1) / T(12));
+    // 3 sum_i w_i c_i chi(x + c_i): axis neighbours weigh 3/9, diagonals 3/36
+    const V gx = R::fma(R::sub(cCr, cCl), third, R::mul(R::add(R::sub(cNr, cNl), R::sub(cSr, cSl)), twelfth));
+    const V gy = R::fma(R::sub(cNc, cSc), third, R::mul(R::sub(R::add(cNr, cNl), R::add(cSr, cSl)), twelfth));
+    const V inv = R::map(R::fma(gx, gx, R::mul(gy, gy)), [&](T g2) { return inv_norm(g2, a.delta); });
+    const V nxv = R::mul(gx, inv), nyv = R::mul(gy, inv);
+    V S;
+    if (MODEL == MODEL_MODIFIED) {
+        const V pc = R::map(ph, [](T q) { return clip01(q); });
+        const V th = R::mul(R::fma(R::c(T(2)), pc, R::c(T(-1))), R::c(a.inv1p2d));
+        S = R::mul(R::fma(R::neg(th), th, R::c(T(1))), R::c(a.inv4eps));
+    } else {
+        S = R::mul(R::mul(ph, R::sub(R::c(T(1)), ph)), R::c(a.inv_eps));
+    }
+    V dx = R::c(T(0)), dy = R::c(T(0));
+    if (!a.first) {
+        dx = R::fma(ph, u, R::neg(R::mul(pp, up)));
+        dy = R::fma(ph, v, R::neg(R::mul(pp, vp)));
+    }
+    const V S3 = R::mul(S, third);
+    const V Gx = R::fma(S3, nxv, dx); // bracket of Eq. 11: d_t(phi u) + c_s^2 S n
+    const V Gy = R::fma(S3, nyv, dy);
+    // Eqs. 9-11 folded: f*_i = (1 - omega) f_i + w_i (A + c_i . B) with A = omega phi
+    // and B = 3 (omega phi u + (1 - 1/(2 tau)) G); f*_0 is the remainder phi - sum_{i>=1}
+    // f*_i (sum_i f*_i = phi holds exactly in real arithmetic), so the collision
+    // conserves mass in any precision whatever the rounding of the weights.
+    const V om1 = R::c(T(1) - a.omega);
+    const V A = R::mul(R::c(a.omega), ph);
+    const V fp = R::c(a.fpref), three = R::c(T(3));
+    const V Bx = R::mul(three, R::fma(A, u, R::mul(fp, Gx)));
+    const V By = R::mul(three, R::fma(A, v, R::mul(fp, Gy)));
+    const V w1 = R::c(w_of<T>(1)), w5 = R::c(w_of<T>(5));
+    fs[1] = R::fma(f[1], om1, R::mul(w1, R::add(A, Bx)));
+    fs[2] = R::fma(f[2], om1, R::mul(w1, R::add(A, By)));
+    fs[3] = R::fma(f[3], om1, R::mul(w1, R::sub(A, Bx)));
+    fs[4] = R::fma(f[4], om1, R::mul(w1, R::sub(A, By)));
+    const V Bp = R::add(Bx, By), Bm = R::sub(Bx, By);
+    fs[5] = R::fma(f[5], om1, R::mul(w5, R::add(A, Bp)));
+    fs[6] = R::fma(f[6], om1, R::mul(w5, R::sub(A, Bm)));
+    fs[7] = R::fma(f[7], om1, R::mul(w5, R::sub(A, Bp)));
+    fs[8] = R::fma(f[8], om1, R::mul(w5, R::add(A, Bm)));
+    V rest = fs[1];
+#pragma unroll
+    for (int i = 2; i < 9; ++i) rest = R::add(rest, fs[i]);
+    fs[0] = R::sub(ph, rest);
+}
+
+// Steps a4-a12 for one node (x, yc) with T arithmetic: collide_core, then the 9
+// stores of f* (or, when `out` is given, the values written there for the caller).
+// cS/cC/cN point at column x - 1 of rows yc - 1, yc, yc + 1 of the chi ring.
 template <typename T, int MODEL, class Vel>
 __device__ __forceinline__ void collide_node_row(const StepArgs<T>& a, const Vel& vel, const typename Vel::Col& vcol,
                                                  const typename Vel::Row& vrow, int x, int yc, const T* f, T ph,
                                                  T pp, const T* cS, const T* cC, const T* cN, bool store = true,
                                                  T* out = nullptr)
 {
-    const T third = T(1) / T(3), twelfth = T(1) / T(12);
-    // 3 sum_i w_i c_i chi(x + c_i): axis neighbours weigh 3/9, diagonals 3/36
-    const T gx = (cC[2] - cC[0]) * third + ((cN[2] - cN[0]) + (cS[2] - cS[0])) * twelfth;
-    const T gy = (cN[1] - cS[1]) * third + ((cN[2] + cN[0]) - (cS[2] + cS[0])) * twelfth;
-    const T inv = inv_norm(gx * gx + gy * gy, a.delta);
-    const T nxv = gx * inv, nyv = gy * inv;
-    T S;
-    if (MODEL == MODEL_MODIFIED) {
-        const T pc = ph < T(0) ? T(0) : (ph > T(1) ? T(1) : ph);
-        const T th = (T(2) * pc - T(1)) * a.inv1p2d;
-        S = (T(1) - th * th) * a.inv4eps;
-    } else {
-        S = ph * (T(1) - ph) * a.inv_eps;
-    }
     T u, v, up, vp;
     vel.at(vcol, vrow, u, v, up, vp);
-    T dx = T(0), dy = T(0);
-    if (!a.first) {
-        dx = ph * u - pp * up;
-        dy = ph * v - pp * vp;
-    }
-    const T Gx = dx + S * nxv * third; // bracket of Eq. 11: d_t(phi u) + c_s^2 S n
-    const T Gy = dy + S * nyv * third;
-    // Eqs. 9-11 folded: f*_i = (1 - omega) f_i + w_i (A + c_i . B) with A = omega phi
-    // and B = 3 (omega phi u + (1 - 1/(2 tau)) G); f*_0 is the remainder phi - sum_{i>=1}
-    // f*_i (sum_i f*_i = phi holds exactly in real arithmetic), so the collision
-    // conserves mass in any precision whatever the rounding of the weights.
-    const T om1 = T(1) - a.omega;
-    const T A = a.omega * ph;
-    const T Bx = T(3) * (A * u + a.fpref * Gx);
-    const T By = T(3) * (A * v + a.fpref * Gy);
-    const T w1 = w_of<T>(1), w5 = w_of<T>(5);
     T fs[9];
-    fs[1] = f[1] * om1 + w1 * (A + Bx);
-    fs[2] = f[2] * om1 + w1 * (A + By);
-    fs[3] = f[3] * om1 + w1 * (A - Bx);
-    fs[4] = f[4] * om1 + w1 * (A - By);
-    const T Bp = Bx + By, Bm = Bx - By;
-    fs[5] = f[5] * om1 + w5 * (A + Bp);
-    fs[6] = f[6] * om1 + w5 * (A - Bm);
-    fs[7] = f[7] * om1 + w5 * (A - Bp);
-    fs[8] = f[8] * om1 + w5 * (A + Bm);
-    T rest = T(0);
-#pragma unroll
-    for (int i = 1; i < 9; ++i) rest += fs[i];
-    fs[0] = ph - rest;
+    collide_core<T, T, MODEL>(a, f, ph, pp, cS[0], cS[1], cS[2], cC[0], cC[2], cN[0], cN[1], cN[2], u, v, up, vp, fs);
     if (out) {
 #pragma unroll
         for (int i = 0; i < 9; ++i) out[i] = fs[i];
@@ -249,6 +308,42 @@ __device__ __forceinline__ void collide_node_row(const StepArgs<T>& a, const Vel
         const unsigned o = (unsigned)yc * (unsigned)a.nx + (unsigned)x;
 #pragma unroll
         for (int i = 0; i < 9; ++i) a.fout[o + (unsigned)i * (unsigned)a.plane] = fs[i];
+    }
+}
+
+// Two adjacent nodes (xa, xa + 1) of row yc: collide_core on float2 (packed FP32x2)
+// for FP32, twice on double for FP64. rS/rC/rN point at column xa - 1 of rows yc - 1,
+// yc, yc + 1 (four consecutive ring entries). Writes f* of both nodes as pairs.
+template <typename T, int MODEL, class Vel>
+__device__ __forceinline__ void collide_pair(const StepArgs<T>& a, const Vel& vel, const typename Vel::Col& ca,
+                                             const typename Vel::Col& cb, const typename Vel::Row& vra,
+                                             const typename Vel::Row& vrb, const T* fa, const T* fb, T pha, T phb,
+                                             T ppa, T ppb, const T* rS, const T* rC, const T* rN,
+                                             typename Pair2<T>::type* out)
+{
+    T ua, va, upa, vpa, ub, vb, upb, vpb;
+    vel.at(ca, vra, ua, va, upa, vpa);
+    vel.at(cb, vrb, ub, vb, upb, vpb);
+    if constexpr (sizeof(T) == 4) {
+        float2 f2[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) f2[i] = make_float2(fa[i], fb[i]);
+        collide_core<float2, float, MODEL>(
+            a, f2, make_float2(pha, phb), make_float2(ppa, ppb), make_float2(rS[0], rS[1]), make_float2(rS[1], rS[2]),
+            make_float2(rS[2], rS[3]), make_float2(rC[0], rC[1]), make_float2(rC[2], rC[3]), make_float2(rN[0], rN[1]),
+            make_float2(rN[1], rN[2]), make_float2(rN[2], rN[3]), make_float2(ua, ub), make_float2(va, vb),
+            make_float2(upa, upb), make_float2(vpa, vpb), out);
+    } else {
+        T oa[9], ob[9];
+        collide_core<T, T, MODEL>(a, fa, pha, ppa, rS[0], rS[1], rS[2], rC[0], rC[2], rN[0], rN[1], rN[2], ua, va, upa,
+                                  vpa, oa);
+        collide_core<T, T, MODEL>(a, fb, phb, ppb, rS[1], rS[2], rS[3], rC[1], rC[3], rN[1], rN[2], rN[3], ub, vb, upb,
+                                  vpb, ob);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            out[i].x = oa[i];
+            out[i].y = ob[i];
+        }
     }
 }
 

@@ -24,10 +24,6 @@ namespace lbmace {
 constexpr int PAIR_THREADS = 128;
 constexpr int PAIR_COLS = 2 * PAIR_THREADS;
 
-template <typename T> struct Pair2;
-template <> struct Pair2<float> { using type = float2; };
-template <> struct Pair2<double> { using type = double2; };
-
 template <typename T, int MODEL, class Vel>
 __global__ void __launch_bounds__(PAIR_THREADS, sizeof(T) == 4 ? 5 : 1) ace_step_pair(const StepArgs<T> a, const Vel vel)
 {
@@ -148,9 +144,19 @@ __global__ void __launch_bounds__(PAIR_THREADS, sizeof(T) == 4 ? 5 : 1) ace_step
         T fa[9], fb[9];
         unpack(nxt, fa, fb);
         const T hvk = hv;
-        T sa = T(0), sb = T(0);
+        T sa, sb; // phi of both nodes, summed in order 0..8 like every other variant
+        if constexpr (sizeof(T) == 4) {
+            float2 s2 = make_float2(0.0f, 0.0f);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) { sa += fa[i]; sb += fb[i]; }
+            for (int i = 0; i < 9; ++i) s2 = __fadd2_rn(s2, make_float2(fa[i], fb[i]));
+            sa = s2.x;
+            sb = s2.y;
+        } else {
+            sa = T(0);
+            sb = T(0);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) { sa += fa[i]; sb += fb[i]; }
+        }
         if (act) {
             V c2;
             c2.x = chi_of<T, MODEL>(sa, a);
@@ -172,22 +178,13 @@ __global__ void __launch_bounds__(PAIR_THREADS, sizeof(T) == 4 ? 5 : 1) ace_step
         if (k >= 2) {
             const int yc = y0 + k - 2;
             const int j = act ? 2 * tx : w - 2; // ring column of xa - 1 is j + 1
-            const T* cS = chi_s[(k - 2) & 3] + 1 + j;
-            const T* cC = chi_s[(k - 1) & 3] + 1 + j;
-            const T* cN = chi_s[k & 3] + 1 + j;
-            T oa[9], ob[9];
-            collide_node_row<T, MODEL>(a, vel, ca, vr, xa, yc, pa, pha, ppa, cS, cC, cN, false, oa);
-            collide_node_row<T, MODEL>(a, vel, cb, vel.rowv(cb, xb, yc), xb, yc, pb, phb, ppb, cS + 1, cC + 1,
-                                       cN + 1, false, ob);
+            V o2[9];
+            collide_pair<T, MODEL>(a, vel, ca, cb, vr, vel.rowv(cb, xb, yc), pa, pb, pha, phb, ppa, ppb,
+                                   chi_s[(k - 2) & 3] + 1 + j, chi_s[(k - 1) & 3] + 1 + j, chi_s[k & 3] + 1 + j, o2);
             if (act) {
                 const unsigned o = (unsigned)yc * nxu + (unsigned)xa;
 #pragma unroll
-                for (int i = 0; i < 9; ++i) {
-                    V s2;
-                    s2.x = oa[i];
-                    s2.y = ob[i];
-                    *reinterpret_cast<V*>(a.fout + (o + (unsigned)i * plane)) = s2;
-                }
+                for (int i = 0; i < 9; ++i) *reinterpret_cast<V*>(a.fout + (o + (unsigned)i * plane)) = o2[i];
                 V p2;
                 p2.x = pha;
                 p2.y = phb;

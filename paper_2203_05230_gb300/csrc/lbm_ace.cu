@@ -8,6 +8,7 @@
 #include "ace_step_bulk.cuh"
 #include "ace_step_warp.cuh"
 #include "ace_step_pair.cuh"
+#include "ace_step_dev.cuh"
 
 #include <cuda_runtime.h>
 
@@ -47,7 +48,9 @@ struct lbm_ace_ctx {
     size_t elem = 0;        // bytes per stored value
     void* f[2] = {nullptr, nullptr};
     int cur = 0;            // buffer holding f*(t-1)
-    void* phi = nullptr;    // phi(t-1) plane
+    void* phi = nullptr;    // phi(t-1) plane (deviation storage: phi2[pcur])
+    float* phi2[2] = {nullptr, nullptr}; // deviation storage: ping-pong FP32 phi planes
+    int pcur = 0;
     double* step_part = nullptr; int n_step_part = 0;
     double* red_part = nullptr; int n_red_part = 0;
     double* result = nullptr;
@@ -180,6 +183,78 @@ void launch_step_t(lbm_ace_ctx* c)
     else launch_step_m<T, MODEL_CONSERVATIVE>(c);
 }
 
+template <typename S>
+DevArgs<S> make_dev(lbm_ace_ctx* c)
+{
+    DevArgs<S> d;
+    d.gin = (const unsigned short*)c->f[c->cur];
+    d.gout = (unsigned short*)c->f[1 - c->cur];
+    d.phin = c->phi2[c->pcur];
+    d.phout = c->phi2[1 - c->pcur];
+    return d;
+}
+
+template <typename S, int MODEL, class Vel>
+void launch_dev_k(lbm_ace_ctx* c, const Vel& vel)
+{
+    dim3 grid(c->grid_x, c->grid_y);
+    StepArgs<float> a = make_args<float>(c);
+    ace_step_dev<S, MODEL, Vel><<<grid, PAIR_THREADS, 0, c->stream>>>(make_dev<S>(c), a, vel);
+}
+
+template <typename S, int MODEL>
+void launch_dev_m(lbm_ace_ctx* c)
+{
+    switch (c->p.velocity_kind) {
+    case LBM_ACE_VEL_SINGLE_VORTEX: launch_dev_k<S, MODEL>(c, vortex<float>(c, (double)c->t)); break;
+    case LBM_ACE_VEL_UNIFORM: {
+        VelUniform<float> v; v.ux = float(c->p.ux); v.uy = float(c->p.uy);
+        launch_dev_k<S, MODEL>(c, v);
+        break;
+    }
+    default: launch_dev_k<S, MODEL>(c, planes<float>(c)); break;
+    }
+}
+
+template <typename S>
+void launch_dev_s(lbm_ace_ctx* c)
+{
+    if (c->p.model == LBM_ACE_MODEL_MODIFIED) launch_dev_m<S, MODEL_MODIFIED>(c);
+    else launch_dev_m<S, MODEL_CONSERVATIVE>(c);
+}
+
+void launch_step_any(lbm_ace_ctx* c)
+{
+    switch (c->p.precision) {
+    case LBM_ACE_F64: launch_step_t<double>(c); break;
+    case LBM_ACE_F32: launch_step_t<float>(c); break;
+    case LBM_ACE_F16DEV: launch_dev_s<__half>(c); break;
+    default: launch_dev_s<__nv_bfloat16>(c); break;
+    }
+}
+
+template <typename S>
+void launch_init_dev(lbm_ace_ctx* c, const double* dphi0)
+{
+    const long long n = (long long)c->p.nx * c->p.ny;
+    const int g = grid_for(n, c->sms);
+    unsigned short* gs = (unsigned short*)c->f[c->cur];
+    float* phi = c->phi2[c->pcur];
+    switch (c->p.velocity_kind) {
+    case LBM_ACE_VEL_SINGLE_VORTEX:
+        ace_init_dev<S><<<g, 256, 0, c->stream>>>(dphi0, gs, phi, c->p.nx, c->p.ny, vortex<float>(c, 0.0));
+        break;
+    case LBM_ACE_VEL_UNIFORM: {
+        VelUniform<float> v; v.ux = float(c->p.ux); v.uy = float(c->p.uy);
+        ace_init_dev<S><<<g, 256, 0, c->stream>>>(dphi0, gs, phi, c->p.nx, c->p.ny, v);
+        break;
+    }
+    default:
+        ace_init_dev<S><<<g, 256, 0, c->stream>>>(dphi0, gs, phi, c->p.nx, c->p.ny, planes<float>(c));
+        break;
+    }
+}
+
 template <typename T>
 void launch_init_t(lbm_ace_ctx* c, const double* dphi0)
 {
@@ -265,6 +340,32 @@ int occupancy_m(lbm_ace_ctx* c, int* blocks)
     }
 }
 
+template <typename S, int MODEL, class Vel>
+int occupancy_dev_k(lbm_ace_ctx* c, int* blocks)
+{
+    c->smem = 0;
+    c->tile_x = PAIR_COLS;
+    CK(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, ace_step_dev<S, MODEL, Vel>, PAIR_THREADS, 0));
+    return LBM_ACE_OK;
+}
+
+template <typename S, int MODEL>
+int occupancy_dev_m(lbm_ace_ctx* c, int* blocks)
+{
+    switch (c->p.velocity_kind) {
+    case LBM_ACE_VEL_SINGLE_VORTEX: return occupancy_dev_k<S, MODEL, VelVortex<float>>(c, blocks);
+    case LBM_ACE_VEL_UNIFORM: return occupancy_dev_k<S, MODEL, VelUniform<float>>(c, blocks);
+    default: return occupancy_dev_k<S, MODEL, VelPlanes<float>>(c, blocks);
+    }
+}
+
+template <typename S>
+int occupancy_dev(lbm_ace_ctx* c, int* blocks)
+{
+    return c->p.model == LBM_ACE_MODEL_MODIFIED ? occupancy_dev_m<S, MODEL_MODIFIED>(c, blocks)
+                                                : occupancy_dev_m<S, MODEL_CONSERVATIVE>(c, blocks);
+}
+
 template <typename T>
 int occupancy_t(lbm_ace_ctx* c, int* blocks)
 {
@@ -273,6 +374,7 @@ int occupancy_t(lbm_ace_ctx* c, int* blocks)
 }
 
 bool is_f64(const lbm_ace_ctx* c) { return c->p.precision == LBM_ACE_F64; }
+bool is_dev(const lbm_ace_ctx* c) { return c->p.precision == LBM_ACE_F16DEV || c->p.precision == LBM_ACE_BF16DEV; }
 
 int ensure_scratch(lbm_ace_ctx* c, size_t elems)
 {
@@ -373,7 +475,8 @@ void lbm_ace_destroy(lbm_ace_ctx* c)
     if (!c) return;
     DeviceGuard g(c->dev);
     if (c->stream) cudaStreamSynchronize(c->stream); else cudaDeviceSynchronize();
-    void* bufs[] = {c->f[0], c->f[1], c->phi, c->step_part, c->red_part, c->result, c->scratch, c->dev_err,
+    void* bufs[] = {c->f[0], c->f[1], c->phi, c->phi2[0], c->phi2[1], c->step_part, c->red_part, c->result,
+                    c->scratch, c->dev_err,
                     c->vel.sx2, c->vel.s2x, c->vel.sy2, c->vel.s2y,
                     c->vel.pu[0], c->vel.pu[1], c->vel.pv[0], c->vel.pv[1]};
     for (void* b : bufs) if (b) cudaFree(b);
@@ -390,11 +493,16 @@ static int init_impl(lbm_ace_ctx* c, const lbm_ace_params* p)
     CK(c, cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->dev));
     const int nx = p->nx, ny = p->ny;
     const size_t n = (size_t)nx * ny;
-    c->elem = is_f64(c) ? sizeof(double) : sizeof(float);
+    c->elem = is_f64(c) ? sizeof(double) : (is_dev(c) ? 2 : sizeof(float));
 
     CK(c, cudaMalloc(&c->f[0], 9 * n * c->elem));
     CK(c, cudaMalloc(&c->f[1], 9 * n * c->elem));
-    CK(c, cudaMalloc(&c->phi, n * c->elem));
+    if (is_dev(c)) {
+        CK(c, cudaMalloc(&c->phi2[0], n * sizeof(float)));
+        CK(c, cudaMalloc(&c->phi2[1], n * sizeof(float)));
+    } else {
+        CK(c, cudaMalloc(&c->phi, n * c->elem));
+    }
     CK(c, cudaMalloc(&c->result, 2 * sizeof(double)));
 
     CK(c, cudaMalloc(&c->dev_err, sizeof(int)));
@@ -404,10 +512,17 @@ static int init_impl(lbm_ace_ctx* c, const lbm_ace_params* p)
     // automatic choice: column pairs when nx is even (fastest measured on GB300 at
     // 2048^2), else direct loads
     c->variant = p->kernel_variant != 0 ? p->kernel_variant : (nx % 2 == 0 ? 4 : 1);
+    if (is_dev(c)) c->variant = 5; // the deviation-storage kernel (column pairs)
 
     // launch shape of the fused step: one wave of resident CTAs when possible
     int occ = 0;
-    int rc = is_f64(c) ? occupancy_t<double>(c, &occ) : occupancy_t<float>(c, &occ);
+    int rc;
+    switch (p->precision) {
+    case LBM_ACE_F64: rc = occupancy_t<double>(c, &occ); break;
+    case LBM_ACE_F32: rc = occupancy_t<float>(c, &occ); break;
+    case LBM_ACE_F16DEV: rc = occupancy_dev<__half>(c, &occ); break;
+    default: rc = occupancy_dev<__nv_bfloat16>(c, &occ); break;
+    }
     if (rc) return rc;
     if (occ < 1) occ = 1;
     c->grid_x = (nx + c->tile_x - 1) / c->tile_x;
@@ -431,7 +546,7 @@ static int init_impl(lbm_ace_ctx* c, const lbm_ace_params* p)
 
     // velocity
     if (p->velocity_kind == LBM_ACE_VEL_SINGLE_VORTEX) {
-        rc = is_f64(c) ? fill_vortex_tables<double>(c) : fill_vortex_tables<float>(c);
+        rc = is_f64(c) ? fill_vortex_tables<double>(c) : fill_vortex_tables<float>(c); // FP32 for 16-bit storage
         if (rc) return rc;
     } else if (p->velocity_kind == LBM_ACE_VEL_FIELD || p->velocity_kind == LBM_ACE_VEL_CALLBACK) {
         const int pairs = p->velocity_kind == LBM_ACE_VEL_CALLBACK ? 2 : 1;
@@ -468,7 +583,13 @@ static int init_impl(lbm_ace_ctx* c, const lbm_ace_params* p)
     }
     c->cur = 0;
     c->t = 0;
-    if (is_f64(c)) launch_init_t<double>(c, c->scratch); else launch_init_t<float>(c, c->scratch);
+    c->pcur = 0;
+    switch (p->precision) {
+    case LBM_ACE_F64: launch_init_t<double>(c, c->scratch); break;
+    case LBM_ACE_F32: launch_init_t<float>(c, c->scratch); break;
+    case LBM_ACE_F16DEV: launch_init_dev<__half>(c, c->scratch); break;
+    default: launch_init_dev<__nv_bfloat16>(c, c->scratch); break;
+    }
     CK(c, cudaGetLastError());
     CK(c, cudaStreamSynchronize(c->stream));
     return LBM_ACE_OK;
@@ -489,8 +610,12 @@ int lbm_ace_init(const lbm_ace_params* p, lbm_ace_ctx** out)
         if (std::fabs(p->M - m) > 1e-12 * m)
             return fail(nullptr, LBM_ACE_EINVAL, "M = %.17g differs from c_s^2 (tau - 0.5) = %.17g", p->M, m);
     }
-    if (p->precision != LBM_ACE_F64 && p->precision != LBM_ACE_F32)
-        return fail(nullptr, LBM_ACE_EINVAL, "precision %d is not available in this build", p->precision);
+    if (p->precision < LBM_ACE_F64 || p->precision > LBM_ACE_BF16DEV)
+        return fail(nullptr, LBM_ACE_EINVAL, "precision %d unknown", p->precision);
+    if ((p->precision == LBM_ACE_F16DEV || p->precision == LBM_ACE_BF16DEV) && p->nx % 2 != 0)
+        return fail(nullptr, LBM_ACE_EINVAL, "16-bit deviation storage needs an even nx (nx = %d)", p->nx);
+    if ((p->precision == LBM_ACE_F16DEV || p->precision == LBM_ACE_BF16DEV) && p->kernel_variant != 0)
+        return fail(nullptr, LBM_ACE_EINVAL, "16-bit deviation storage has one step kernel; kernel_variant must be 0");
     if (p->model != LBM_ACE_MODEL_MODIFIED && p->model != LBM_ACE_MODEL_CONSERVATIVE)
         return fail(nullptr, LBM_ACE_EINVAL, "model %d unknown", p->model);
     switch (p->velocity_kind) {
@@ -560,9 +685,10 @@ int lbm_ace_step(lbm_ace_ctx* c, long long n)
             if (rc) return rc;
             c->vel.cur = next;
         }
-        if (is_f64(c)) launch_step_t<double>(c); else launch_step_t<float>(c);
+        launch_step_any(c);
         CK(c, cudaGetLastError());
         c->cur = 1 - c->cur;
+        if (is_dev(c)) c->pcur = 1 - c->pcur;
         c->t += 1;
         c->stepped = true;
     }
@@ -578,8 +704,18 @@ int lbm_ace_get_phi(lbm_ace_ctx* c, double* out, size_t count)
     int rc = ensure_scratch(c, n);
     if (rc) return rc;
     const int gr = grid_for((long long)n, c->sms);
-    if (is_f64(c)) ace_moment<double><<<gr, 256, 0, c->stream>>>((const double*)c->f[c->cur], c->scratch, c->p.nx, c->p.ny);
-    else ace_moment<float><<<gr, 256, 0, c->stream>>>((const float*)c->f[c->cur], c->scratch, c->p.nx, c->p.ny);
+    const unsigned short* gs = (const unsigned short*)c->f[c->cur];
+    switch (c->p.precision) {
+    case LBM_ACE_F64: ace_moment<double><<<gr, 256, 0, c->stream>>>((const double*)c->f[c->cur], c->scratch, c->p.nx, c->p.ny); break;
+    case LBM_ACE_F32: ace_moment<float><<<gr, 256, 0, c->stream>>>((const float*)c->f[c->cur], c->scratch, c->p.nx, c->p.ny); break;
+    case LBM_ACE_F16DEV:
+        ace_pull_state_dev<__half><<<gr, 256, 0, c->stream>>>(gs, c->phi2[c->pcur], nullptr, c->scratch, nullptr, c->p.nx, c->p.ny);
+        break;
+    default:
+        ace_pull_state_dev<__nv_bfloat16><<<gr, 256, 0, c->stream>>>(gs, c->phi2[c->pcur], nullptr, c->scratch, nullptr,
+                                                                     c->p.nx, c->p.ny);
+        break;
+    }
     CK(c, cudaGetLastError());
     CK(c, cudaMemcpyAsync(out, c->scratch, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
@@ -591,9 +727,18 @@ int lbm_ace_mass(lbm_ace_ctx* c, double* out)
     if (!c) return fail(nullptr, LBM_ACE_EINVAL, "ctx is NULL");
     if (!out) return fail(c, LBM_ACE_EINVAL, "out is NULL");
     DeviceGuard g(c->dev);
-    const long long n9 = 9LL * c->p.nx * c->p.ny;
-    if (is_f64(c)) ace_sum_partials<double><<<c->n_red_part, RED_THREADS, 0, c->stream>>>((const double*)c->f[c->cur], n9, c->red_part);
-    else ace_sum_partials<float><<<c->n_red_part, RED_THREADS, 0, c->stream>>>((const float*)c->f[c->cur], n9, c->red_part);
+    const long long n = (long long)c->p.nx * c->p.ny, n9 = 9 * n;
+    const unsigned short* gs = (const unsigned short*)c->f[c->cur];
+    switch (c->p.precision) {
+    case LBM_ACE_F64: ace_sum_partials<double><<<c->n_red_part, RED_THREADS, 0, c->stream>>>((const double*)c->f[c->cur], n9, c->red_part); break;
+    case LBM_ACE_F32: ace_sum_partials<float><<<c->n_red_part, RED_THREADS, 0, c->stream>>>((const float*)c->f[c->cur], n9, c->red_part); break;
+    case LBM_ACE_F16DEV:
+        ace_sum_partials_dev<__half><<<c->n_red_part, RED_THREADS, 0, c->stream>>>(gs, c->phi2[c->pcur], n, c->red_part);
+        break;
+    default:
+        ace_sum_partials_dev<__nv_bfloat16><<<c->n_red_part, RED_THREADS, 0, c->stream>>>(gs, c->phi2[c->pcur], n, c->red_part);
+        break;
+    }
     CK(c, cudaGetLastError());
     const int rc = finalize_sum(c, c->red_part, c->n_red_part, out);
     if (rc) return rc;
@@ -621,12 +766,25 @@ int lbm_ace_get_state(lbm_ace_ctx* c, double* f, double* phi_prev)
     int rc = ensure_scratch(c, 10 * n);
     if (rc) return rc;
     const int gr = grid_for((long long)n, c->sms);
-    if (is_f64(c))
+    const unsigned short* gs = (const unsigned short*)c->f[c->cur];
+    switch (c->p.precision) {
+    case LBM_ACE_F64:
         ace_pull_state<double><<<gr, 256, 0, c->stream>>>((const double*)c->f[c->cur], (const double*)c->phi,
                                                           c->scratch, c->scratch + 9 * n, c->p.nx, c->p.ny);
-    else
+        break;
+    case LBM_ACE_F32:
         ace_pull_state<float><<<gr, 256, 0, c->stream>>>((const float*)c->f[c->cur], (const float*)c->phi,
                                                          c->scratch, c->scratch + 9 * n, c->p.nx, c->p.ny);
+        break;
+    case LBM_ACE_F16DEV:
+        ace_pull_state_dev<__half><<<gr, 256, 0, c->stream>>>(gs, c->phi2[c->pcur], c->scratch, nullptr,
+                                                              c->scratch + 9 * n, c->p.nx, c->p.ny);
+        break;
+    default:
+        ace_pull_state_dev<__nv_bfloat16><<<gr, 256, 0, c->stream>>>(gs, c->phi2[c->pcur], c->scratch, nullptr,
+                                                                     c->scratch + 9 * n, c->p.nx, c->p.ny);
+        break;
+    }
     CK(c, cudaGetLastError());
     if (f) CK(c, cudaMemcpyAsync(f, c->scratch, 9 * n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     if (phi_prev) CK(c, cudaMemcpyAsync(phi_prev, c->scratch + 9 * n, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -650,12 +808,25 @@ int lbm_ace_set_state(lbm_ace_ctx* c, const double* f, const double* phi_prev, l
     CK(c, cudaMemcpyAsync(c->scratch, f, 9 * n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     CK(c, cudaMemcpyAsync(c->scratch + 9 * n, phi_prev, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     const int gr = grid_for((long long)n, c->sms);
-    if (is_f64(c))
+    unsigned short* gs = (unsigned short*)c->f[c->cur];
+    switch (c->p.precision) {
+    case LBM_ACE_F64:
         ace_push_state<double><<<gr, 256, 0, c->stream>>>(c->scratch, c->scratch + 9 * n, (double*)c->f[c->cur],
                                                           (double*)c->phi, c->p.nx, c->p.ny);
-    else
+        break;
+    case LBM_ACE_F32:
         ace_push_state<float><<<gr, 256, 0, c->stream>>>(c->scratch, c->scratch + 9 * n, (float*)c->f[c->cur],
                                                          (float*)c->phi, c->p.nx, c->p.ny);
+        break;
+    case LBM_ACE_F16DEV:
+        ace_push_state_dev<__half><<<gr, 256, 0, c->stream>>>(c->scratch, c->scratch + 9 * n, gs, c->phi2[c->pcur],
+                                                              c->p.nx, c->p.ny);
+        break;
+    default:
+        ace_push_state_dev<__nv_bfloat16><<<gr, 256, 0, c->stream>>>(c->scratch, c->scratch + 9 * n, gs,
+                                                                     c->phi2[c->pcur], c->p.nx, c->p.ny);
+        break;
+    }
     CK(c, cudaGetLastError());
     CK(c, cudaStreamSynchronize(c->stream));
     c->t = t;

@@ -1,0 +1,101 @@
+"""16-bit deviation storage (FP16 / BF16) against the FP64 oracle, through the C ABI.
+
+The library stores g_i = f*_i - s_i phi in 16 bits (s: dyadic split weights summing
+to 1) and does all arithmetic in FP32. Tolerances follow from the storage rounding:
+the deviations are at most ~0.02 in these states, so one rounding costs ~1e-5 (FP16,
+11-bit significand) or ~8e-5 (BF16, 8-bit) absolute; one step is checked against
+5e-5 (FP16) and 4e-4 (BF16) of max|f|. Over the full 256^2 single-vortex period the
+phi-L2 error against the oracle is bounded and printed.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2203_05230_gb300 import lbm_ace as A
+from paper_2203_05230_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+DEV = [(A.F16DEV, 5e-5), (A.BF16DEV, 4e-4)]
+
+
+def rel_max(a, b):
+    return np.abs(a - b).max() / np.abs(b).max()
+
+
+@pytest.mark.parametrize("precision,tol", DEV)
+@pytest.mark.parametrize("nx,ny,model", [(64, 64, 0), (258, 37, 0), (514, 21, 1), (4, 9, 0)])
+def test_dev_one_step_close_to_oracle(precision, tol, nx, ny, model):
+    op = O.Params(nx=nx, ny=ny, tau=0.8, eps=1.0, U0=0.05, T=100.0, sign=-1.0, model=model)
+    s = O.Sim(op, W.random_smooth_phi(nx, ny, seed=nx + ny)).step(3)
+    with A.Lattice(nx=nx, ny=ny, tau=0.8, eps=1.0, U0=0.05, T_period=100.0, vortex_sign=-1.0,
+                   model=model, precision=precision) as g:
+        g.set_state(s.f, s.phi_prev, s.t)
+        f_in, pp_in = g.get_state()          # the state as stored (rounded to 16 bits)
+        assert rel_max(f_in, s.f) <= tol and np.array_equal(pp_in, s.phi_prev.astype(np.float32))
+        g.step(1)
+        f, pp = g.get_state()
+    ref = O.Sim.from_state(op, f_in, pp_in, s.t).step(1)  # oracle from the stored state
+    assert rel_max(f, ref.f) <= tol
+    assert rel_max(pp, ref.phi_prev) <= 1e-6  # phi(t) itself is FP32
+
+
+@pytest.mark.parametrize("precision,bound,mbound", [(A.F16DEV, 2e-4, 5e-5), (A.BF16DEV, 5e-3, 1e-3)])
+def test_dev_full_period_256_phi_l2_and_mass(precision, bound, mbound):
+    """Single vortex on 256^2 (T = 4096, eps 1) against the FP64 oracle: phi-L2 after the
+    full period (printed; measured 3.8e-5 FP16, 1.0e-3 BF16), and the mass drift left by
+    rounding the deviations to 16 bits (unbiased, so it grows like a random walk:
+    measured 5.6e-6 FP16, 2.2e-4 BF16 over the period)."""
+    v = W.vortex_fp32(256)
+    phi0 = v.phi0()
+    op = O.Params(nx=256, ny=256, tau=v.tau, eps=v.eps, U0=v.U0, T=v.T, sign=v.sign)
+    ref = O.Sim(op, phi0).step(v.T, threads=O.threads_available()).phi()
+    with A.Lattice(nx=256, ny=256, tau=v.tau, eps=v.eps, U0=v.U0, T_period=float(v.T),
+                   vortex_sign=v.sign, precision=precision, phi0=phi0) as g:
+        m0 = g.mass()
+        g.step(v.T)
+        phi = g.phi()
+        m1 = g.mass()
+        ms = g.step_mass()
+    e2 = math.sqrt(((phi - ref) ** 2).sum() / (ref ** 2).sum())
+    drift = (m1 - m0) / m0
+    print(f"precision {precision}: phi-L2 vs FP64 oracle after one period = {e2:.3e}, "
+          f"mass drift = {drift:.3e}")
+    assert e2 <= bound
+    assert abs(drift) <= mbound
+    assert ms == pytest.approx(m1, rel=1e-5)
+
+
+@pytest.mark.parametrize("precision", [A.F16DEV, A.BF16DEV])
+def test_dev_phi_readout_matches_state(precision):
+    """get_phi returns the moment of the populations get_state returns."""
+    with A.vortex_lattice(128, precision=precision) as g:
+        g.step(37)
+        f, _ = g.get_state()
+        phi = g.phi()
+    assert np.abs(f.sum(0) - phi).max() <= 2e-6
+
+
+@pytest.mark.parametrize("precision", [A.F16DEV, A.BF16DEV])
+def test_dev_resume_from_checkpoint(precision):
+    """A run resumed from get_state / set_state follows the uninterrupted run to the
+    storage rounding (the checkpoint goes through FP64 populations)."""
+    with A.vortex_lattice(128, precision=precision) as a:
+        a.step(30)
+        f, pp = a.get_state()
+        a.step(30)
+        pa = a.phi()
+    with A.vortex_lattice(128, precision=precision) as b:
+        b.set_state(f, pp, 30)
+        b.step(30)
+        pb = b.phi()
+    assert np.abs(pa - pb).max() <= (2e-5 if precision == A.F16DEV else 2e-4)
+
+
+def test_dev_rejects_odd_nx_and_variants():
+    with pytest.raises(A.LbmAceError):
+        A.Lattice(nx=65, ny=64, precision=A.F16DEV)
+    with pytest.raises(A.LbmAceError):
+        A.Lattice(nx=64, ny=64, precision=A.BF16DEV, kernel_variant=1)
