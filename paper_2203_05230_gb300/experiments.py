@@ -1,0 +1,128 @@
+"""Accuracy studies on the GPU library (single-vortex benchmark of Section 3).
+
+Everything here runs through the C ABI; numpy only computes the error measures of
+the results (phi-L1/L2 against a reference field, mass drift, interface width).
+
+* ``paper_ablation``: the paper's own run (Section 3: L = 200, R = 0.2 L at
+  (0.5 L, 0.75 L), U0 = 0.04, M = 0.001, T = 6 L / U0 = 30000 steps, the sign of
+  Eq. 14) for the modified ACE (Eq. 8) and the conservative-ACE ablation (Eq. 1),
+  over several interface thicknesses: the relative L1 error of phi(T) against phi(0)
+  (the quantity of Fig. 2, whose data the paper does not include).
+* ``fp32_study``: FP32 against the FP64 GPU path over one period on the FP32
+  workloads (1024^2 and 2048^2, eps in {0.5, 1, 2}, T = 16 L).
+* ``precision_study``: FP64, FP32, FP16- and BF16-deviation storage on 4096^2
+  (eps 1, T = 16384): phi-L2 against FP64, mass drift, interface width, speed.
+
+Run: python -m paper_2203_05230_gb300.experiments {ablation,fp32,precision} (one GPU).
+The paper's eps is 4x the eps used here (psi = eps ln(phi / (1 - phi)) as printed
+in Eq. 13); tables give both.
+"""
+from __future__ import annotations
+
+import json
+import math
+import sys
+import time
+
+import numpy as np
+
+from . import lbm_ace as A
+from . import workloads as W
+
+
+def errors(phi: np.ndarray, ref: np.ndarray) -> dict:
+    """Relative L1 and L2 errors of phi against ref."""
+    d = phi - ref
+    return {"E1": float(np.abs(d).sum() / np.abs(ref).sum()),
+            "E2": float(math.sqrt((d * d).sum() / (ref * ref).sum()))}
+
+
+def interface_width(phi: np.ndarray, band=(0.05, 0.95)) -> float:
+    """sum phi(1 - phi) / sum |grad phi| over the nodes of the interface band (central
+    differences, periodic). For the equilibrium profile 1/2 + 1/2 tanh(s / (2 eps)),
+    phi(1 - phi) = eps |dphi/ds|, so the ratio is eps over any band; restricting it to
+    the band keeps rounding noise in the bulk (where both sums would otherwise gather
+    small contributions from millions of nodes) out of the estimate."""
+    gx = 0.5 * (np.roll(phi, -1, axis=1) - np.roll(phi, 1, axis=1))
+    gy = 0.5 * (np.roll(phi, -1, axis=0) - np.roll(phi, 1, axis=0))
+    m = (phi > band[0]) & (phi < band[1])
+    return float((phi * (1 - phi))[m].sum() / np.sqrt(gx * gx + gy * gy)[m].sum())
+
+
+def run_vortex(L, *, eps, tau, U0, T, steps=None, precision=A.F64, model=A.MODEL_MODIFIED, sign=-1.0,
+               R_frac=0.15, yc_frac=0.75):
+    """Run the single vortex for `steps` (default T) steps; returns (phi0, phi, mass0, mass,
+    seconds of the stepping)."""
+    v = W.Vortex(L=L, eps=eps, tau=tau, U0=U0, T=int(T), R_frac=R_frac, yc_frac=yc_frac, sign=sign)
+    phi0 = v.phi0()
+    with A.Lattice(nx=L, ny=L, tau=tau, eps=eps, U0=U0, T_period=float(T), vortex_sign=sign,
+                   precision=precision, model=model, phi0=phi0) as g:
+        m0 = g.mass()
+        g.synchronize()
+        t0 = time.perf_counter()
+        g.step(int(steps if steps is not None else T))
+        g.synchronize()
+        dt = time.perf_counter() - t0
+        phi = g.phi()
+        m1 = g.mass()
+    return phi0, phi, m0, m1, dt
+
+
+def paper_ablation(eps_paper=(1.5, 2.0, 3.0, 4.0), precision=A.F64):
+    L, U0, M = 200, 0.04, 0.001
+    tau = 0.5 + 3.0 * M
+    T = int(round(6 * L / U0))
+    rows = []
+    for ep in eps_paper:
+        row = {"eps_paper": ep, "eps": ep / 4}
+        for name, model in (("modified", A.MODEL_MODIFIED), ("conservative", A.MODEL_CONSERVATIVE)):
+            phi0, phi, m0, m1, _ = run_vortex(L, eps=ep / 4, tau=tau, U0=U0, T=T, precision=precision,
+                                              model=model, sign=1.0, R_frac=0.2, yc_frac=0.75)
+            e = errors(phi, phi0)
+            row[name] = {"E1": e["E1"], "E2": e["E2"], "mass_drift": (m1 - m0) / m0,
+                         "phi_min": float(phi.min()), "phi_max": float(phi.max())}
+        rows.append(row)
+    return {"study": "paper single vortex, L 200, R 40 at (100, 150), U0 0.04, M 0.001 (tau 0.503), "
+                     "T 30000 steps, Eq. 14 sign; relative L1/L2 of phi(T) against phi(0)",
+            "precision": int(precision), "rows": rows}
+
+
+def fp32_study(sizes=(1024, 2048), eps_list=(0.5, 1.0, 2.0)):
+    rows = []
+    for L in sizes:
+        for eps in eps_list:
+            v = W.vortex_fp32(L, eps)
+            kw = dict(eps=eps, tau=v.tau, U0=v.U0, T=v.T)
+            phi0, p64, a0, a1, t64 = run_vortex(L, precision=A.F64, **kw)
+            _, p32, b0, b1, t32 = run_vortex(L, precision=A.F32, **kw)
+            rows.append({"L": L, "eps": eps, "T": v.T,
+                         "fp32_vs_fp64": errors(p32, p64),
+                         "shape_return_fp64": errors(p64, phi0), "shape_return_fp32": errors(p32, phi0),
+                         "mass_drift_fp64": (a1 - a0) / a0, "mass_drift_fp32": (b1 - b0) / b0,
+                         "mlups_fp64": L * L * v.T / t64 / 1e6, "mlups_fp32": L * L * v.T / t32 / 1e6})
+    return {"study": "FP32 against the FP64 GPU path over one single-vortex period (T = 16 L)", "rows": rows}
+
+
+def precision_study(L=4096, T=16384, eps=1.0):
+    kw = dict(eps=eps, tau=0.8, U0=0.04, T=T)
+    out = {}
+    phi0 = ref = None
+    for name, prec in (("f64", A.F64), ("f32", A.F32), ("f16dev", A.F16DEV), ("bf16dev", A.BF16DEV)):
+        p0, phi, m0, m1, dt = run_vortex(L, precision=prec, **kw)
+        if ref is None:
+            phi0, ref = p0, phi
+        out[name] = {"vs_fp64": errors(phi, ref), "shape_return": errors(phi, phi0),
+                     "mass_drift": (m1 - m0) / m0, "width_t0": interface_width(phi0),
+                     "width_T": interface_width(phi), "mlups": L * L * T / dt / 1e6}
+    return {"study": f"single vortex {L}x{L}, eps {eps}, tau 0.8, U0 0.04, T {T}: storage forms against "
+                     "the FP64 GPU run", "forms": out}
+
+
+def main(argv):
+    which = argv[1] if len(argv) > 1 else "ablation"
+    res = {"ablation": paper_ablation, "fp32": fp32_study, "precision": precision_study}[which]()
+    print(json.dumps(res))
+
+
+if __name__ == "__main__":
+    main(sys.argv)

@@ -400,3 +400,14 @@ def test_rounding_sensitivity_at_saturated_phi_sets_the_multi_step_bound():
     s.step(19)
     b.step(19)
     assert np.abs(s.phi() - b.phi()).max() < d1
+
+
+def test_banded_interface_width_estimator_returns_eps():
+    """The width estimator used by the accuracy studies gives eps for the Eq. 2 profile
+    (phi(1 - phi) = eps |dphi/ds|) and ignores rounding-level noise in the bulk."""
+    from paper_2203_05230_gb300 import experiments as X
+    for eps in (1.0, 2.0):
+        phi = W.disk_phi0(512, 512, 256.0, 256.0, 150.0, eps)
+        assert X.interface_width(phi) == pytest.approx(eps, rel=3e-3)
+        noisy = phi + 1e-4 * np.random.default_rng(0).standard_normal(phi.shape)
+        assert X.interface_width(noisy) == pytest.approx(eps, rel=2e-2)
