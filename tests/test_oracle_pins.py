@@ -404,10 +404,12 @@ def test_rounding_sensitivity_at_saturated_phi_sets_the_multi_step_bound():
 
 def test_banded_interface_width_estimator_returns_eps():
     """The width estimator used by the accuracy studies gives eps for the Eq. 2 profile
-    (phi(1 - phi) = eps |dphi/ds|) and ignores rounding-level noise in the bulk."""
+    (phi(1 - phi) = eps |dphi/ds|) up to the O(1/eps^2) error of central differences
+    (1.2 % at eps = 1 lattice unit, 0.02 % at eps = 8), and ignores rounding-level
+    noise in the bulk."""
     from paper_2203_05230_gb300 import experiments as X
-    for eps in (1.0, 2.0):
+    for eps in (1.0, 2.0, 4.0, 8.0):
         phi = W.disk_phi0(512, 512, 256.0, 256.0, 150.0, eps)
-        assert X.interface_width(phi) == pytest.approx(eps, rel=3e-3)
+        assert abs(X.interface_width(phi) / eps - 1) < 0.015 / eps ** 2
         noisy = phi + 1e-4 * np.random.default_rng(0).standard_normal(phi.shape)
-        assert X.interface_width(noisy) == pytest.approx(eps, rel=2e-2)
+        assert abs(X.interface_width(noisy) / eps - 1) < 0.015 / eps ** 2
