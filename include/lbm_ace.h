@@ -65,9 +65,9 @@ enum {
 enum {
     LBM_ACE_F64 = 0,    /* FP64 populations, FP64 arithmetic */
     LBM_ACE_F32 = 1,    /* FP32 populations, FP32 arithmetic, FP64 mass sums */
-    LBM_ACE_F16DEV = 2, /* populations stored as FP16 deviations g_i = f*_i - s_i phi from split
-                           weights s = (1820, 455 x4, 114 x4)/4096 (close to the D2Q9
-                           weights, summing exactly to 1), phi in FP32, FP32 arithmetic,
+    LBM_ACE_F16DEV = 2, /* populations stored as FP16 deviations g_i = f*_i - s_i phi, with
+                           split weights s = (1820, 455 x4, 114 x4)/4096 (close to the D2Q9
+                           weights, summing exactly to 1); phi in FP32, FP32 arithmetic,
                            44 bytes per node update; needs an even nx */
     LBM_ACE_BF16DEV = 3 /* as above with BF16 storage */
 };
@@ -179,6 +179,53 @@ int lbm_ace_launch_shape(const lbm_ace_ctx* c, int* tile_x, int* rows_per_cta, i
 
 /* Block until all device work of the context has finished. */
 int lbm_ace_synchronize(lbm_ace_ctx* c);
+
+/* ---- Batches: many independent single-vortex lattices advanced together ----------
+ * Each lattice of a batch is a single-vortex problem (Section 3, Eq. 14) with its own
+ * size, disk, eps, tau, U0 and period, FP32 populations, and one model for the whole
+ * batch. A batch step advances every lattice by one time step with one launch of a
+ * persistent kernel (one CTA per resident slot pulling tiles of all lattices from a
+ * work counter), replayed from a captured CUDA graph; the time t is shared. The
+ * batch owns its device memory and works on params[0].stream (or on a stream of its
+ * own when that is NULL, since graphs cannot be captured on the legacy stream). */
+typedef struct lbm_ace_batch lbm_ace_batch;
+
+/* Build a batch of `count` lattices from params[0..count-1]. Each needs precision
+ * LBM_ACE_F32, velocity LBM_ACE_VEL_SINGLE_VORTEX, an even nx, phi0 == NULL (the disk
+ * from xc, yc, R is built on the device), the same model; rows_per_cta sets the tile
+ * height of that lattice (0: 64; at least 8 is used). Device and stream come from
+ * params[0]. */
+int lbm_ace_batch_init(const lbm_ace_params* params, int count, lbm_ace_batch** out);
+
+/* Advance every lattice by n >= 0 steps: n replays of the captured {step, advance}
+ * graph. Asynchronous on the batch's stream. */
+int lbm_ace_batch_step(lbm_ace_batch* b, long long n);
+
+/* The same n steps as one ordinary launch per lattice per step (the single-lattice
+ * column-pair kernel in the launch shape the single-lattice library picks, host-side
+ * loop): the baseline a batch is compared with. Synchronous. */
+int lbm_ace_batch_step_sequential(lbm_ace_batch* b, long long n);
+
+/* Choose the tile height of each lattice size by coordinate descent over {8, 16, 32,
+ * 64, 128, 256}, timing steps_per_trial batch steps per trial with CUDA events; the
+ * lattices' states and time are saved before and restored after the trials. Writes
+ * the chosen heights to rows_out[count] when not NULL. Allocates a copy of the state
+ * for the duration of the call. */
+int lbm_ace_batch_autotune(lbm_ace_batch* b, int steps_per_trial, int* rows_out);
+
+/* phi(x, t) of lattice i (host out[count], count == nx*ny of that lattice). Synchronous. */
+int lbm_ace_batch_get_phi(lbm_ace_batch* b, int i, double* out, size_t count);
+
+/* Global mass of lattice i (compensated FP64 sum on the device). Synchronous. */
+int lbm_ace_batch_mass(lbm_ace_batch* b, int i, double* out);
+
+/* Tile height of lattice i, total tiles per step, persistent grid size, total nodes. */
+int lbm_ace_batch_info(const lbm_ace_batch* b, int i, int* rows, int* tiles, int* grid, long long* nodes);
+
+long long lbm_ace_batch_steps_done(const lbm_ace_batch* b);
+int lbm_ace_batch_synchronize(lbm_ace_batch* b);
+const char* lbm_ace_batch_last_error(const lbm_ace_batch* b);
+void lbm_ace_batch_destroy(lbm_ace_batch* b); /* NULL-safe */
 
 /* Allocation-free global mass, for callers that cannot allocate device memory (the
  * paper has no counterpart; it is a service of this library). Some callers cannot

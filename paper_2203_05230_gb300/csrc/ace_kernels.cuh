@@ -588,7 +588,7 @@ __global__ void __launch_bounds__(RED_THREADS) ace_sum_partials(const T* __restr
 
 // Final sum of n partials by one warp: per-lane compensated sums over a strided
 // subset, then lane 0 combines the 32 (sum, compensation) pairs in lane order.
-__global__ void ace_finalize(const double* __restrict__ part, int n, double* __restrict__ out)
+static __global__ void ace_finalize(const double* __restrict__ part, int n, double* __restrict__ out)
 {
     const int lane = threadIdx.x;
     double s = 0.0, c = 0.0;

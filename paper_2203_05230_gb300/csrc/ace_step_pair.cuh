@@ -24,17 +24,18 @@ namespace lbmace {
 constexpr int PAIR_THREADS = 128;
 constexpr int PAIR_COLS = 2 * PAIR_THREADS;
 
+// One tile: columns [x0, x0 + 256) (clipped to nx) and rows [y0, y0 + a.rows) of the
+// lattice described by `a`. chi_s (4 x (PAIR_COLS + 4), 16-byte aligned: ring index j
+// holds column x0 + j - 2) and red_s (PAIR_THREADS / 32 doubles) are the CTA's shared
+// memory; thread 0 writes the tile's FP64 mass of phi(t) to *mass_out. Ends with a
+// barrier, so the CTA can take another tile right after.
 template <typename T, int MODEL, class Vel>
-__global__ void __launch_bounds__(PAIR_THREADS, sizeof(T) == 4 ? 5 : 1) ace_step_pair(const StepArgs<T> a, const Vel vel)
+__device__ __forceinline__ void pair_tile(const StepArgs<T>& a, const Vel& vel, int x0, int y0,
+                                          T (*chi_s)[PAIR_COLS + 4], double* red_s, double* mass_out)
 {
     using V = typename Pair2<T>::type;
-    // ring index j holds column x0 + j - 2: j = 1 left halo, 2 .. w + 1 own, w + 2 right halo
-    __shared__ __align__(16) T chi_s[4][PAIR_COLS + 4];
-    __shared__ double red_s[PAIR_THREADS / 32];
-
     const int tx = threadIdx.x;
     const int lane = tx & 31;
-    const int x0 = blockIdx.x * PAIR_COLS;
     const int w = min(PAIR_COLS, a.nx - x0); // even
     const bool act = 2 * tx < w;
     const int xa = x0 + (act ? 2 * tx : w - 2); // threads past a ragged edge redo the last pair
@@ -43,7 +44,6 @@ __global__ void __launch_bounds__(PAIR_THREADS, sizeof(T) == 4 ? 5 : 1) ace_step
     const int xr = xb == a.nx - 1 ? 0 : xb + 1;     // column right of the pair
     const bool own_left = lane == 0;                // no lane to the left in this warp
     const bool own_right = lane == 31 || 2 * (tx + 1) >= w; // no active lane to the right
-    const int y0 = blockIdx.y * a.rows;
     const int y1 = min(y0 + a.rows, a.ny);
     const int nk = y1 - y0 + 2;
     const unsigned nxu = (unsigned)a.nx, plane = (unsigned)a.plane;
@@ -206,8 +206,18 @@ __global__ void __launch_bounds__(PAIR_THREADS, sizeof(T) == 4 ? 5 : 1) ace_step
         double s = 0.0;
 #pragma unroll
         for (int i = 0; i < PAIR_THREADS / 32; ++i) s += red_s[i];
-        a.mass_part[(long long)blockIdx.y * gridDim.x + blockIdx.x] = s;
+        *mass_out = s;
     }
+    __syncthreads();
+}
+
+template <typename T, int MODEL, class Vel>
+__global__ void __launch_bounds__(PAIR_THREADS, sizeof(T) == 4 ? 5 : 1) ace_step_pair(const StepArgs<T> a, const Vel vel)
+{
+    __shared__ __align__(16) T chi_s[4][PAIR_COLS + 4];
+    __shared__ double red_s[PAIR_THREADS / 32];
+    pair_tile<T, MODEL>(a, vel, blockIdx.x * PAIR_COLS, blockIdx.y * a.rows, chi_s, red_s,
+                        &a.mass_part[(long long)blockIdx.y * gridDim.x + blockIdx.x]);
 }
 
 } // namespace lbmace

@@ -13,7 +13,10 @@ the results (phi-L1/L2 against a reference field, mass drift, interface width).
 * ``precision_study``: FP64, FP32, FP16- and BF16-deviation storage on 4096^2
   (eps 1, T = 16384): phi-L2 against FP64, mass drift, interface width, speed.
 
-Run: python -m paper_2203_05230_gb300.experiments {ablation,fp32,precision} (one GPU).
+* ``batch_study``: 256 lattices of uneven size in one persistent, graph-replayed
+  launch per step (tiles from the autotuner) against one launch per lattice per step.
+
+Run: python -m paper_2203_05230_gb300.experiments {ablation,fp32,precision,batch} (one GPU).
 The paper's eps is 4x the eps used here (psi = eps ln(phi / (1 - phi)) as printed
 in Eq. 13); tables give both.
 """
@@ -118,9 +121,46 @@ def precision_study(L=4096, T=16384, eps=1.0):
                      "the FP64 GPU run", "forms": out}
 
 
+def batch_specs(count=256, seed=0):
+    """The batched workload: `count` single-vortex lattices with seeded draws (sides
+    from {128, ..., 1024}, centre in [0.3, 0.7] L, radius in [0.1, 0.2] L, eps in
+    [0.5, 2], tau in [0.6, 1.0], U0 in [0.02, 0.05], T in [8 L, 16 L])."""
+    return [dict(nx=q.L, ny=q.L, xc=q.xc, yc=q.yc, R=q.R, eps=q.eps, tau=q.tau, U0=q.U0,
+                 T_period=float(q.T), vortex_sign=-1.0) for q in W.batched_instances(count, seed)]
+
+
+def batch_study(count=256, steps=20, tune_steps=3):
+    """Aggregate MLUPS of the persistent graph-replayed batch (after autotuning) against
+    one launch per lattice per step, on the same lattices."""
+    specs = batch_specs(count)
+    with A.Batch(specs) as b:
+        nodes = b.info()["nodes"]
+        t0 = time.perf_counter()
+        rows = b.autotune(steps_per_trial=tune_steps)
+        tune_s = time.perf_counter() - t0
+        b.step(3)
+        b.synchronize()
+        t0 = time.perf_counter()
+        b.step(steps)
+        b.synchronize()
+        dt_g = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        b.step_sequential(steps)
+        dt_s = time.perf_counter() - t0
+        info = b.info()
+    sides = sorted({s["nx"] for s in specs})
+    return {"study": f"{count} single-vortex lattices, sides {sides}, FP32", "nodes": nodes,
+            "tiles": info["tiles"], "grid": info["grid"], "autotune_s": tune_s,
+            "rows_by_side": {int(s["nx"]): r for s, r in zip(specs, rows)},
+            "mlups_batched_graph": nodes * steps / dt_g / 1e6,
+            "mlups_sequential_launches": nodes * steps / dt_s / 1e6,
+            "speedup": dt_s / dt_g}
+
+
 def main(argv):
     which = argv[1] if len(argv) > 1 else "ablation"
-    res = {"ablation": paper_ablation, "fp32": fp32_study, "precision": precision_study}[which]()
+    res = {"ablation": paper_ablation, "fp32": fp32_study, "precision": precision_study,
+           "batch": batch_study}[which]()
     print(json.dumps(res))
 
 

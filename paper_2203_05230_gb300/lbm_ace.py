@@ -38,6 +38,9 @@ EXPORTS = (
     "lbm_ace_step_mass", "lbm_ace_get_state", "lbm_ace_set_state", "lbm_ace_steps_done",
     "lbm_ace_launch_shape", "lbm_ace_synchronize", "lbm_ace_last_error", "lbm_ace_status_string",
     "lbm_ace_destroy", "lbm_ace_mass_noalloc",
+    "lbm_ace_batch_init", "lbm_ace_batch_step", "lbm_ace_batch_step_sequential", "lbm_ace_batch_autotune",
+    "lbm_ace_batch_get_phi", "lbm_ace_batch_mass", "lbm_ace_batch_info", "lbm_ace_batch_steps_done",
+    "lbm_ace_batch_synchronize", "lbm_ace_batch_last_error", "lbm_ace_batch_destroy",
 )
 NOALLOC_CHUNK = 65536
 NOALLOC_MAX_PARTIALS = 4096
@@ -107,6 +110,25 @@ def load(build_if_missing: bool = True):
     L.lbm_ace_destroy.restype = None
     L.lbm_ace_mass_noalloc.argtypes = [_P, ctypes.c_int, ctypes.c_longlong, _P, _P]
     L.lbm_ace_mass_noalloc.restype = ctypes.c_int
+    _I = ctypes.POINTER(ctypes.c_int)
+    L.lbm_ace_batch_init.argtypes = [ctypes.POINTER(lbm_ace_params), ctypes.c_int, ctypes.POINTER(_P)]
+    L.lbm_ace_batch_step.argtypes = [_P, ctypes.c_longlong]
+    L.lbm_ace_batch_step_sequential.argtypes = [_P, ctypes.c_longlong]
+    L.lbm_ace_batch_autotune.argtypes = [_P, ctypes.c_int, _I]
+    L.lbm_ace_batch_get_phi.argtypes = [_P, ctypes.c_int, _D, ctypes.c_size_t]
+    L.lbm_ace_batch_mass.argtypes = [_P, ctypes.c_int, _D]
+    L.lbm_ace_batch_info.argtypes = [_P, ctypes.c_int, _I, _I, _I, ctypes.POINTER(ctypes.c_longlong)]
+    L.lbm_ace_batch_steps_done.argtypes = [_P]
+    L.lbm_ace_batch_steps_done.restype = ctypes.c_longlong
+    L.lbm_ace_batch_synchronize.argtypes = [_P]
+    L.lbm_ace_batch_last_error.argtypes = [_P]
+    L.lbm_ace_batch_last_error.restype = ctypes.c_char_p
+    L.lbm_ace_batch_destroy.argtypes = [_P]
+    L.lbm_ace_batch_destroy.restype = None
+    for name in ("lbm_ace_batch_init", "lbm_ace_batch_step", "lbm_ace_batch_step_sequential",
+                 "lbm_ace_batch_autotune", "lbm_ace_batch_get_phi", "lbm_ace_batch_mass",
+                 "lbm_ace_batch_info", "lbm_ace_batch_synchronize"):
+        getattr(L, name).restype = ctypes.c_int
     for name in ("lbm_ace_params_default", "lbm_ace_init", "lbm_ace_step", "lbm_ace_get_phi",
                  "lbm_ace_mass", "lbm_ace_step_mass", "lbm_ace_get_state", "lbm_ace_set_state",
                  "lbm_ace_launch_shape", "lbm_ace_synchronize"):
@@ -251,6 +273,93 @@ class Lattice:
             self.ctx = None
 
     lbm_ace_destroy = close
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class Batch:
+    """Many single-vortex lattices advanced together (wraps lbm_ace_batch_*).
+
+    ``lattices`` is a list of dicts of ``lbm_ace_params`` fields (nx, ny, tau, eps, U0,
+    T_period, vortex_sign, xc, yc, R, rows_per_cta, ...); precision FP32 and the single
+    vortex are set here. ``stream`` as for Lattice."""
+
+    def __init__(self, lattices, stream=None, device=0, model=MODEL_MODIFIED):
+        self._lib = load()
+        arr = (lbm_ace_params * len(lattices))()
+        for k, kw in enumerate(lattices):
+            self._lib.lbm_ace_params_default(ctypes.byref(arr[k]))
+            arr[k].precision = F32
+            arr[k].velocity_kind = VEL_SINGLE_VORTEX
+            arr[k].model = model
+            arr[k].device = device
+            if stream is not None:
+                arr[k].stream = ctypes.c_void_p(int(getattr(stream, "cuda_stream", stream)))
+            for f, v in kw.items():
+                setattr(arr[k], f, v)
+        self.shapes = [(int(p.ny), int(p.nx)) for p in arr]
+        h = _P()
+        rc = self._lib.lbm_ace_batch_init(arr, len(lattices), ctypes.byref(h))
+        if rc != OK:
+            raise LbmAceError(rc, (self._lib.lbm_ace_batch_last_error(None) or b"").decode(errors="replace"))
+        self.h = h
+
+    def _check(self, rc):
+        if rc != OK:
+            raise LbmAceError(rc, (self._lib.lbm_ace_batch_last_error(self.h) or b"").decode(errors="replace"))
+
+    def step(self, n=1):
+        self._check(self._lib.lbm_ace_batch_step(self.h, int(n)))
+        return self
+
+    def step_sequential(self, n=1):
+        self._check(self._lib.lbm_ace_batch_step_sequential(self.h, int(n)))
+        return self
+
+    def autotune(self, steps_per_trial=5):
+        rows = (ctypes.c_int * len(self.shapes))()
+        self._check(self._lib.lbm_ace_batch_autotune(self.h, int(steps_per_trial), rows))
+        return list(rows)
+
+    def phi(self, i):
+        ny, nx = self.shapes[i]
+        out = np.empty((ny, nx))
+        self._check(self._lib.lbm_ace_batch_get_phi(self.h, int(i), _dp(out), out.size))
+        return out
+
+    def mass(self, i):
+        m = ctypes.c_double()
+        self._check(self._lib.lbm_ace_batch_mass(self.h, int(i), ctypes.byref(m)))
+        return m.value
+
+    def info(self, i=0):
+        r, t, g = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        n = ctypes.c_longlong()
+        self._check(self._lib.lbm_ace_batch_info(self.h, int(i), ctypes.byref(r), ctypes.byref(t),
+                                                 ctypes.byref(g), ctypes.byref(n)))
+        return {"rows": r.value, "tiles": t.value, "grid": g.value, "nodes": n.value}
+
+    @property
+    def t(self):
+        return int(self._lib.lbm_ace_batch_steps_done(self.h))
+
+    def synchronize(self):
+        self._check(self._lib.lbm_ace_batch_synchronize(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.lbm_ace_batch_destroy(self.h)
+            self.h = None
 
     def __del__(self):
         try:

@@ -1,0 +1,86 @@
+"""Batches of single-vortex lattices (persistent kernel, CUDA graph, autotuner).
+
+Every lattice of a batch must evolve exactly as the same lattice would alone: the
+batched kernel runs the same per-tile code (pair_tile); the only difference is where
+the phase cos(pi t / T) of Eq. 14 is computed (on the device in the graph, on the host
+for single lattices), which can move its last FP32 bit, hence the 1e-6 bound.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2203_05230_gb300 import lbm_ace as A
+from paper_2203_05230_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+SPECS = [dict(nx=128, ny=128, tau=0.7, eps=0.8, U0=0.03, T_period=1500.0, xc=60.0, yc=70.0, R=20.0),
+         dict(nx=192, ny=160, tau=0.9, eps=1.5, U0=0.05, T_period=2200.0, xc=90.0, yc=100.0, R=30.0),
+         dict(nx=256, ny=256, tau=0.65, eps=1.0, U0=0.02, T_period=3000.0, xc=120.0, yc=140.0, R=40.0),
+         dict(nx=384, ny=96, tau=0.8, eps=2.0, U0=0.04, T_period=3100.0, xc=200.0, yc=50.0, R=25.0),
+         dict(nx=130, ny=41, tau=1.0, eps=0.6, U0=0.045, T_period=900.0, xc=60.0, yc=20.0, R=10.0)]
+
+
+def standalone(spec, steps):
+    with A.Lattice(precision=A.F32, velocity_kind=A.VEL_SINGLE_VORTEX, vortex_sign=-1.0, **spec) as g:
+        m0 = g.mass()
+        g.step(steps)
+        return g.phi(), m0, g.mass()
+
+
+@pytest.mark.parametrize("rows", [0, 8, 33])
+def test_batch_lattices_evolve_as_alone(rows):
+    specs = [dict(s, rows_per_cta=rows, vortex_sign=-1.0) for s in SPECS]
+    with A.Batch(specs) as b:
+        b.step(57)
+        assert b.t == 57
+        for i, s in enumerate(SPECS):
+            ref, m0, m1 = standalone(s, 57)
+            assert np.abs(b.phi(i) - ref).max() <= 1e-6
+            assert b.mass(i) == pytest.approx(m1, rel=1e-6)
+            assert abs(b.mass(i) - m0) <= 1e-5 * m0
+
+
+def test_graph_steps_match_sequential_launches():
+    specs = [dict(s, vortex_sign=-1.0) for s in SPECS]
+    with A.Batch(specs) as a, A.Batch(specs) as b:
+        a.step(40)
+        b.step_sequential(25)
+        b.step(15)  # mixing the two modes keeps the device time in step
+        assert a.t == b.t == 40
+        for i in range(len(SPECS)):
+            assert np.abs(a.phi(i) - b.phi(i)).max() <= 1e-6
+
+
+def test_autotune_keeps_the_state_and_picks_candidate_heights():
+    specs = [dict(s, vortex_sign=-1.0) for s in SPECS]
+    with A.Batch(specs) as b:
+        b.step(10)
+        before = [b.phi(i) for i in range(len(SPECS))]
+        rows = b.autotune(steps_per_trial=2)
+        assert b.t == 10
+        for i, s in enumerate(SPECS):
+            assert rows[i] in (8, 16, 32, 64, 128, 256) or rows[i] == s["ny"]
+            assert np.array_equal(b.phi(i), before[i])
+        b.step(20)
+        for i, s in enumerate(SPECS):
+            ref, _, _ = standalone(s, 30)
+            assert np.abs(b.phi(i) - ref).max() <= 1e-6
+
+
+def test_batch_lattice_close_to_oracle():
+    """One lattice of a batch against the FP64 oracle over 40 steps (FP32 storage)."""
+    s = SPECS[0]
+    phi0 = W.disk_phi0(s["nx"], s["ny"], s["xc"], s["yc"], s["R"], s["eps"])
+    p = O.Params(nx=s["nx"], ny=s["ny"], tau=s["tau"], eps=s["eps"], U0=s["U0"], T=s["T_period"], sign=-1.0)
+    ref = O.Sim(p, phi0).step(40).phi()
+    with A.Batch([dict(x, vortex_sign=-1.0) for x in SPECS]) as b:
+        b.step(40)
+        assert np.abs(b.phi(0) - ref).max() <= 2e-5
+
+
+def test_batch_rejects_unsupported_lattices():
+    with pytest.raises(A.LbmAceError):
+        A.Batch([dict(nx=65, ny=64)])
+    with pytest.raises(A.LbmAceError):
+        A.Batch([dict(nx=64, ny=64), dict(nx=64, ny=64, model=A.MODEL_CONSERVATIVE)])
