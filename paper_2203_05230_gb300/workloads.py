@@ -137,3 +137,75 @@ def stream_function_field(n: int, seed: int, modes: int = 4, umax: float = 0.05)
         v -= a * np.cos(arg) * 2 * math.pi * kx / n
     scale = umax * rng.uniform(0.3, 1.0) / max(np.sqrt(u * u + v * v).max(), 1e-30)
     return u * scale, v * scale
+
+
+# Learned surrogate: training trajectories and initial weights.
+SURROGATE_TILE = 256          # periodic tiles of 256 x 256 nodes
+SURROGATE_K = 16              # LB steps per surrogate application
+SURROGATE_WIDTHS = (3, 32, 32, 32, 32, 1)
+
+
+def circles_phi0(n: int, rng: np.random.Generator, eps: float = 1.0) -> np.ndarray:
+    """1-4 disks of radius 0.05-0.2 n at uniform centres on a periodic n x n lattice
+    (minimum-image distance), each with the tanh rim of disk_phi0; phi0 is their
+    pointwise maximum. float64 [n, n]."""
+    y, x = np.mgrid[0:n, 0:n].astype(np.float64)
+    phi = np.zeros((n, n))
+    for _ in range(int(rng.integers(1, 5))):
+        xc, yc = rng.uniform(0, n, size=2)
+        R = rng.uniform(0.05, 0.2) * n
+        dx = (x - xc + 0.5 * n) % n - 0.5 * n
+        dy = (y - yc + 0.5 * n) % n - 0.5 * n
+        r = np.sqrt(dx * dx + dy * dy)
+        phi = np.maximum(phi, 0.5 * (1.0 + np.tanh((R - r) / (2.0 * eps))))
+    return phi
+
+
+def mode_field(n: int, rng: np.random.Generator, modes: int = 4, umax: float = 0.05):
+    """Divergence-free periodic velocity from the stream function
+    chi = sum_m a_m sin(2 pi (kx_m x + ky_m y) / n + p_m) with integer wavenumbers
+    |kx|, |ky| <= 2 (not both 0), a_m standard normal, p_m uniform; u = d(chi)/dy and
+    v = -d(chi)/dx analytically, scaled so that max |(u, v)| is uniform in [0.4, 1] umax.
+    float64 [n, n] each."""
+    y, x = np.mgrid[0:n, 0:n].astype(np.float64)
+    u = np.zeros((n, n))
+    v = np.zeros((n, n))
+    for _ in range(modes):
+        while True:
+            kx, ky = (int(k) for k in rng.integers(-2, 3, size=2))
+            if kx or ky:
+                break
+        a = rng.standard_normal()
+        p = rng.uniform(0, 2 * math.pi)
+        c = a * np.cos(2 * math.pi * (kx * x + ky * y) / n + p) * 2 * math.pi / n
+        u += c * ky
+        v -= c * kx
+    scale = umax * rng.uniform(0.4, 1.0) / max(float(np.sqrt(u * u + v * v).max()), 1e-30)
+    return u * scale, v * scale
+
+
+def surrogate_trajectories(count: int, n: int = SURROGATE_TILE, seed: int = 0):
+    """`count` seeded (PCG64) trajectory starts: (phi0, u, v) with 1-4 circles (eps 1)
+    in a frozen 4-mode divergence-free field of max speed <= 0.05."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for _ in range(count):
+        phi0 = circles_phi0(n, rng)
+        u, v = mode_field(n, rng)
+        out.append((phi0, u, v))
+    return out
+
+
+def surrogate_init_params(widths=SURROGATE_WIDTHS, seed: int = 0) -> np.ndarray:
+    """Initial weights as one flat float64 vector (W_1, b_1, ..., W_L, b_L; each W in
+    [co][ci][row offset][column offset] order): normal with standard deviation
+    sqrt(2 / (9 ci)) for the GELU layers and 0.1 sqrt(1 / (9 ci)) for the output layer,
+    zero biases."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    parts = []
+    nl = len(widths) - 1
+    for l, (ci, co) in enumerate(zip(widths[:-1], widths[1:])):
+        sd = math.sqrt(2.0 / (9 * ci)) if l < nl - 1 else 0.1 * math.sqrt(1.0 / (9 * ci))
+        parts.append(rng.standard_normal(co * ci * 9) * sd)
+        parts.append(np.zeros(co))
+    return np.concatenate(parts)
