@@ -180,6 +180,35 @@ int lbm_ace_launch_shape(const lbm_ace_ctx* c, int* tile_x, int* rows_per_cta, i
 /* Block until all device work of the context has finished. */
 int lbm_ace_synchronize(lbm_ace_ctx* c);
 
+/* ---- Device-side access (for a caller that keeps fields on the GPU) ---------------
+ * These three calls are asynchronous on the context's stream and take DEVICE pointers
+ * (on the context's device) to FP32 [ny][nx] arrays that the caller owns; each must
+ * stay valid until the stream has passed the call. A NULL pointer returns
+ * LBM_ACE_EINVAL without device work. */
+
+/* phi(x, t) = sum_i f_i(x, t) (Eq. 12) at the current time, rounded to FP32, into
+ * phi_out. */
+int lbm_ace_get_phi_device(lbm_ace_ctx* c, float* phi_out);
+
+/* The prescribed velocity u(x, t) at time t (in steps; any real t) into u_out and
+ * v_out: the single vortex of Eq. 14 (evaluated in FP64, rounded), the uniform
+ * velocity or the static field. LBM_ACE_EINVAL for the callback mode. */
+int lbm_ace_velocity_device(lbm_ace_ctx* c, double t, float* u_out, float* v_out);
+
+/* Restart the lattice at time t >= 0 from the phase field phi (device, FP32): the
+ * populations become f_i^eq(phi, u(x, t)) (Eq. 10) and phi(t-1) = phi, as at
+ * initialisation, so d_t(phi u) is zero on the first step after the restart. Used to
+ * hand a phase field produced elsewhere (a learned surrogate) back to the lattice
+ * Boltzmann scheme. LBM_ACE_EINVAL for the callback mode. */
+int lbm_ace_reset_device(lbm_ace_ctx* c, const float* phi, long long t);
+
+/* The CUDA stream (cudaStream_t) the context issues its work on. */
+void* lbm_ace_get_stream(const lbm_ace_ctx* c);
+
+/* A copy of the parameters the context was created with (pointers inside refer to the
+ * caller's original arrays and must not be dereferenced after init returned). */
+int lbm_ace_get_params(const lbm_ace_ctx* c, lbm_ace_params* out);
+
 /* ---- Batches: many independent single-vortex lattices advanced together ----------
  * Each lattice of a batch is a single-vortex problem (Section 3, Eq. 14) with its own
  * size, disk, eps, tau, U0 and period, FP32 populations, and one model for the whole

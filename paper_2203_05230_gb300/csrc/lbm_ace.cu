@@ -58,6 +58,7 @@ struct lbm_ace_ctx {
     VelState vel;
     long long t = 0;
     bool stepped = false;
+    bool fresh = true;      // next step is the first after init or a restart: d_t(phi u) = 0
     int rows = 0, grid_x = 0, grid_y = 0;
     int variant = 1;        // 1: ace_step (direct loads), 2: ace_step_bulk
     int tile_x = TILE_X;
@@ -108,7 +109,7 @@ StepArgs<T> make_args(lbm_ace_ctx* c)
     a.nx = c->p.nx; a.ny = c->p.ny;
     a.plane = (long long)c->p.nx * c->p.ny;
     a.rows = c->rows;
-    a.first = c->t == 0;
+    a.first = c->fresh;
     a.omega = T(1.0 / c->p.tau);
     a.fpref = T(1.0 - 0.5 / c->p.tau);
     a.eps = T(c->p.eps);
@@ -234,7 +235,7 @@ void launch_step_any(lbm_ace_ctx* c)
 }
 
 template <typename S>
-void launch_init_dev(lbm_ace_ctx* c, const double* dphi0)
+void launch_init_dev(lbm_ace_ctx* c, const double* dphi0, double t0)
 {
     const long long n = (long long)c->p.nx * c->p.ny;
     const int g = grid_for(n, c->sms);
@@ -242,7 +243,7 @@ void launch_init_dev(lbm_ace_ctx* c, const double* dphi0)
     float* phi = c->phi2[c->pcur];
     switch (c->p.velocity_kind) {
     case LBM_ACE_VEL_SINGLE_VORTEX:
-        ace_init_dev<S><<<g, 256, 0, c->stream>>>(dphi0, gs, phi, c->p.nx, c->p.ny, vortex<float>(c, 0.0));
+        ace_init_dev<S><<<g, 256, 0, c->stream>>>(dphi0, gs, phi, c->p.nx, c->p.ny, vortex<float>(c, t0));
         break;
     case LBM_ACE_VEL_UNIFORM: {
         VelUniform<float> v; v.ux = float(c->p.ux); v.uy = float(c->p.uy);
@@ -256,7 +257,7 @@ void launch_init_dev(lbm_ace_ctx* c, const double* dphi0)
 }
 
 template <typename T>
-void launch_init_t(lbm_ace_ctx* c, const double* dphi0)
+void launch_init_t(lbm_ace_ctx* c, const double* dphi0, double t0)
 {
     const long long n = (long long)c->p.nx * c->p.ny;
     const int g = grid_for(n, c->sms);
@@ -264,7 +265,7 @@ void launch_init_t(lbm_ace_ctx* c, const double* dphi0)
     T* phi = (T*)c->phi;
     switch (c->p.velocity_kind) {
     case LBM_ACE_VEL_SINGLE_VORTEX:
-        ace_init<T><<<g, 256, 0, c->stream>>>(dphi0, fst, phi, c->p.nx, c->p.ny, vortex<T>(c, 0.0));
+        ace_init<T><<<g, 256, 0, c->stream>>>(dphi0, fst, phi, c->p.nx, c->p.ny, vortex<T>(c, t0));
         break;
     case LBM_ACE_VEL_UNIFORM: {
         VelUniform<T> v; v.ux = T(c->p.ux); v.uy = T(c->p.uy);
@@ -429,6 +430,57 @@ struct DeviceGuard {
     ~DeviceGuard() { if (prev >= 0) cudaSetDevice(prev); }
 };
 
+// phi(x, t) of the current state into c->scratch (FP64), on the context's stream.
+int phi_to_scratch(lbm_ace_ctx* c)
+{
+    const size_t n = (size_t)c->p.nx * c->p.ny;
+    int rc = ensure_scratch(c, n);
+    if (rc) return rc;
+    const int gr = grid_for((long long)n, c->sms);
+    const unsigned short* gs = (const unsigned short*)c->f[c->cur];
+    switch (c->p.precision) {
+    case LBM_ACE_F64: ace_moment<double><<<gr, 256, 0, c->stream>>>((const double*)c->f[c->cur], c->scratch, c->p.nx, c->p.ny); break;
+    case LBM_ACE_F32: ace_moment<float><<<gr, 256, 0, c->stream>>>((const float*)c->f[c->cur], c->scratch, c->p.nx, c->p.ny); break;
+    case LBM_ACE_F16DEV:
+        ace_pull_state_dev<__half><<<gr, 256, 0, c->stream>>>(gs, c->phi2[c->pcur], nullptr, c->scratch, nullptr, c->p.nx, c->p.ny);
+        break;
+    default:
+        ace_pull_state_dev<__nv_bfloat16><<<gr, 256, 0, c->stream>>>(gs, c->phi2[c->pcur], nullptr, c->scratch, nullptr,
+                                                                     c->p.nx, c->p.ny);
+        break;
+    }
+    CK(c, cudaGetLastError());
+    return LBM_ACE_OK;
+}
+
+__global__ void ace_narrow(const double* __restrict__ in, float* __restrict__ out, long long n)
+{
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
+        out[k] = (float)in[k];
+}
+
+__global__ void ace_widen(const float* __restrict__ in, double* __restrict__ out, long long n)
+{
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
+        out[k] = (double)in[k];
+}
+
+// u(x, t), v(x, t) of a velocity source, rounded to FP32.
+template <typename T, class Vel>
+__global__ void ace_velocity(Vel vel, int nx, int ny, float* __restrict__ u_out, float* __restrict__ v_out)
+{
+    const long long plane = (long long)nx * ny;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < plane;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(k % nx), y = (int)(k / nx);
+        T u, v, up, vp;
+        const typename Vel::Col cl = vel.col(x);
+        vel.at(cl, vel.rowv(cl, x, y), u, v, up, vp);
+        u_out[k] = (float)u;
+        v_out[k] = (float)v;
+    }
+}
+
 } // namespace
 
 extern "C" {
@@ -585,11 +637,12 @@ static int init_impl(lbm_ace_ctx* c, const lbm_ace_params* p)
     c->t = 0;
     c->pcur = 0;
     switch (p->precision) {
-    case LBM_ACE_F64: launch_init_t<double>(c, c->scratch); break;
-    case LBM_ACE_F32: launch_init_t<float>(c, c->scratch); break;
-    case LBM_ACE_F16DEV: launch_init_dev<__half>(c, c->scratch); break;
-    default: launch_init_dev<__nv_bfloat16>(c, c->scratch); break;
+    case LBM_ACE_F64: launch_init_t<double>(c, c->scratch, 0.0); break;
+    case LBM_ACE_F32: launch_init_t<float>(c, c->scratch, 0.0); break;
+    case LBM_ACE_F16DEV: launch_init_dev<__half>(c, c->scratch, 0.0); break;
+    default: launch_init_dev<__nv_bfloat16>(c, c->scratch, 0.0); break;
     }
+    c->fresh = true;
     CK(c, cudaGetLastError());
     CK(c, cudaStreamSynchronize(c->stream));
     return LBM_ACE_OK;
@@ -691,6 +744,7 @@ int lbm_ace_step(lbm_ace_ctx* c, long long n)
         if (is_dev(c)) c->pcur = 1 - c->pcur;
         c->t += 1;
         c->stepped = true;
+        c->fresh = false;
     }
     return LBM_ACE_OK;
 }
@@ -701,25 +755,89 @@ int lbm_ace_get_phi(lbm_ace_ctx* c, double* out, size_t count)
     const size_t n = (size_t)c->p.nx * c->p.ny;
     if (!out || count != n) return fail(c, LBM_ACE_EINVAL, "out must hold nx*ny = %zu values (got %zu)", n, count);
     DeviceGuard g(c->dev);
-    int rc = ensure_scratch(c, n);
+    const int rc = phi_to_scratch(c);
     if (rc) return rc;
-    const int gr = grid_for((long long)n, c->sms);
-    const unsigned short* gs = (const unsigned short*)c->f[c->cur];
-    switch (c->p.precision) {
-    case LBM_ACE_F64: ace_moment<double><<<gr, 256, 0, c->stream>>>((const double*)c->f[c->cur], c->scratch, c->p.nx, c->p.ny); break;
-    case LBM_ACE_F32: ace_moment<float><<<gr, 256, 0, c->stream>>>((const float*)c->f[c->cur], c->scratch, c->p.nx, c->p.ny); break;
-    case LBM_ACE_F16DEV:
-        ace_pull_state_dev<__half><<<gr, 256, 0, c->stream>>>(gs, c->phi2[c->pcur], nullptr, c->scratch, nullptr, c->p.nx, c->p.ny);
-        break;
-    default:
-        ace_pull_state_dev<__nv_bfloat16><<<gr, 256, 0, c->stream>>>(gs, c->phi2[c->pcur], nullptr, c->scratch, nullptr,
-                                                                     c->p.nx, c->p.ny);
-        break;
-    }
-    CK(c, cudaGetLastError());
     CK(c, cudaMemcpyAsync(out, c->scratch, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
     return check_device_error(c);
+}
+
+int lbm_ace_get_phi_device(lbm_ace_ctx* c, float* phi_out)
+{
+    if (!c) return fail(nullptr, LBM_ACE_EINVAL, "ctx is NULL");
+    if (!phi_out) return fail(c, LBM_ACE_EINVAL, "phi_out is NULL");
+    DeviceGuard g(c->dev);
+    const int rc = phi_to_scratch(c);
+    if (rc) return rc;
+    const long long n = (long long)c->p.nx * c->p.ny;
+    ace_narrow<<<grid_for(n, c->sms), 256, 0, c->stream>>>(c->scratch, phi_out, n);
+    CK(c, cudaGetLastError());
+    return LBM_ACE_OK;
+}
+
+int lbm_ace_velocity_device(lbm_ace_ctx* c, double t, float* u_out, float* v_out)
+{
+    if (!c) return fail(nullptr, LBM_ACE_EINVAL, "ctx is NULL");
+    if (!u_out || !v_out) return fail(c, LBM_ACE_EINVAL, "u_out or v_out is NULL");
+    if (!std::isfinite(t)) return fail(c, LBM_ACE_EINVAL, "t is not finite");
+    if (c->p.velocity_kind == LBM_ACE_VEL_CALLBACK)
+        return fail(c, LBM_ACE_EINVAL, "velocity_device is not available with a velocity callback");
+    DeviceGuard g(c->dev);
+    const long long n = (long long)c->p.nx * c->p.ny;
+    const int gr = grid_for(n, c->sms);
+    const int nx = c->p.nx, ny = c->p.ny;
+    switch (c->p.velocity_kind) {
+    case LBM_ACE_VEL_SINGLE_VORTEX:
+        if (is_f64(c)) ace_velocity<double><<<gr, 256, 0, c->stream>>>(vortex<double>(c, t), nx, ny, u_out, v_out);
+        else ace_velocity<float><<<gr, 256, 0, c->stream>>>(vortex<float>(c, t), nx, ny, u_out, v_out);
+        break;
+    case LBM_ACE_VEL_UNIFORM: {
+        VelUniform<double> v; v.ux = c->p.ux; v.uy = c->p.uy;
+        ace_velocity<double><<<gr, 256, 0, c->stream>>>(v, nx, ny, u_out, v_out);
+        break;
+    }
+    default:
+        ace_velocity<double><<<gr, 256, 0, c->stream>>>(planes<double>(c), nx, ny, u_out, v_out);
+        break;
+    }
+    CK(c, cudaGetLastError());
+    return LBM_ACE_OK;
+}
+
+int lbm_ace_reset_device(lbm_ace_ctx* c, const float* phi, long long t)
+{
+    if (!c) return fail(nullptr, LBM_ACE_EINVAL, "ctx is NULL");
+    if (!phi) return fail(c, LBM_ACE_EINVAL, "phi is NULL");
+    if (t < 0) return fail(c, LBM_ACE_EINVAL, "t = %lld: must be >= 0", t);
+    if (c->p.velocity_kind == LBM_ACE_VEL_CALLBACK)
+        return fail(c, LBM_ACE_EINVAL, "reset_device is not available with a velocity callback");
+    DeviceGuard g(c->dev);
+    const long long n = (long long)c->p.nx * c->p.ny;
+    int rc = ensure_scratch(c, (size_t)n);
+    if (rc) return rc;
+    ace_widen<<<grid_for(n, c->sms), 256, 0, c->stream>>>(phi, c->scratch, n);
+    CK(c, cudaGetLastError());
+    switch (c->p.precision) {
+    case LBM_ACE_F64: launch_init_t<double>(c, c->scratch, (double)t); break;
+    case LBM_ACE_F32: launch_init_t<float>(c, c->scratch, (double)t); break;
+    case LBM_ACE_F16DEV: launch_init_dev<__half>(c, c->scratch, (double)t); break;
+    default: launch_init_dev<__nv_bfloat16>(c, c->scratch, (double)t); break;
+    }
+    CK(c, cudaGetLastError());
+    c->t = t;
+    c->stepped = false;
+    c->fresh = true;
+    return LBM_ACE_OK;
+}
+
+void* lbm_ace_get_stream(const lbm_ace_ctx* c) { return c ? (void*)c->stream : nullptr; }
+
+int lbm_ace_get_params(const lbm_ace_ctx* c, lbm_ace_params* out)
+{
+    if (!c) return fail(nullptr, LBM_ACE_EINVAL, "ctx is NULL");
+    if (!out) return fail(const_cast<lbm_ace_ctx*>(c), LBM_ACE_EINVAL, "out is NULL");
+    *out = c->p;
+    return LBM_ACE_OK;
 }
 
 int lbm_ace_mass(lbm_ace_ctx* c, double* out)
@@ -831,6 +949,7 @@ int lbm_ace_set_state(lbm_ace_ctx* c, const double* f, const double* phi_prev, l
     CK(c, cudaStreamSynchronize(c->stream));
     c->t = t;
     c->stepped = false;
+    c->fresh = t == 0;
     return LBM_ACE_OK;
 }
 

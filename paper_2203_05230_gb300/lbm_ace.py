@@ -1,4 +1,5 @@
-"""Python binding of the C ABI in include/lbm_ace.h (argument marshalling only).
+"""Python binding of the C ABI in include/lbm_ace.h and include/lbm_ace_surrogate.h
+(argument marshalling only).
 
 Every function here forwards to the entry point of the same name in
 ``liblbm_ace.so``; all lattice Boltzmann arithmetic runs in the library's CUDA
@@ -41,7 +42,13 @@ EXPORTS = (
     "lbm_ace_batch_init", "lbm_ace_batch_step", "lbm_ace_batch_step_sequential", "lbm_ace_batch_autotune",
     "lbm_ace_batch_get_phi", "lbm_ace_batch_mass", "lbm_ace_batch_info", "lbm_ace_batch_steps_done",
     "lbm_ace_batch_synchronize", "lbm_ace_batch_last_error", "lbm_ace_batch_destroy",
+    "lbm_ace_get_phi_device", "lbm_ace_velocity_device", "lbm_ace_reset_device", "lbm_ace_get_stream",
+    "lbm_ace_get_params",
+    "lbm_ace_net_create", "lbm_ace_net_set_params", "lbm_ace_net_get_params", "lbm_ace_net_forward",
+    "lbm_ace_net_loss_grad", "lbm_ace_net_adam", "lbm_ace_net_gather", "lbm_ace_net_metrics",
+    "lbm_ace_net_synchronize", "lbm_ace_net_last_error", "lbm_ace_net_destroy", "lbm_ace_hybrid_advance",
 )
+NET_WIDTH, NET_K, NET_PARAMS = 32, 16, 28929
 NOALLOC_CHUNK = 65536
 NOALLOC_MAX_PARTIALS = 4096
 NOALLOC_MAX_COUNT = NOALLOC_CHUNK * NOALLOC_MAX_PARTIALS
@@ -62,6 +69,12 @@ class lbm_ace_params(ctypes.Structure):
         ("device", ctypes.c_int), ("stream", ctypes.c_void_p),
         ("rows_per_cta", ctypes.c_int), ("kernel_variant", ctypes.c_int),
     ]
+
+
+class lbm_ace_hybrid_stats(ctypes.Structure):
+    _fields_ = [("windows", ctypes.c_longlong), ("surrogate_windows", ctypes.c_longlong),
+                ("fallback_windows", ctypes.c_longlong), ("mass0", ctypes.c_double), ("width0", ctypes.c_double),
+                ("max_mass_drift", ctypes.c_double), ("max_width_dev", ctypes.c_double)]
 
 
 class LbmAceError(RuntimeError):
@@ -132,6 +145,37 @@ def load(build_if_missing: bool = True):
     for name in ("lbm_ace_params_default", "lbm_ace_init", "lbm_ace_step", "lbm_ace_get_phi",
                  "lbm_ace_mass", "lbm_ace_step_mass", "lbm_ace_get_state", "lbm_ace_set_state",
                  "lbm_ace_launch_shape", "lbm_ace_synchronize"):
+        getattr(L, name).restype = ctypes.c_int
+    # device-side access
+    L.lbm_ace_get_phi_device.argtypes = [_P, _P]
+    L.lbm_ace_velocity_device.argtypes = [_P, ctypes.c_double, _P, _P]
+    L.lbm_ace_reset_device.argtypes = [_P, _P, ctypes.c_longlong]
+    L.lbm_ace_get_stream.argtypes = [_P]
+    L.lbm_ace_get_stream.restype = _P
+    L.lbm_ace_get_params.argtypes = [_P, ctypes.POINTER(lbm_ace_params)]
+    for name in ("lbm_ace_get_phi_device", "lbm_ace_velocity_device", "lbm_ace_reset_device", "lbm_ace_get_params"):
+        getattr(L, name).restype = ctypes.c_int
+    # surrogate
+    _F = ctypes.POINTER(ctypes.c_float)
+    L.lbm_ace_net_create.argtypes = [ctypes.c_int, _P, ctypes.POINTER(_P)]
+    L.lbm_ace_net_set_params.argtypes = [_P, _F, ctypes.c_size_t]
+    L.lbm_ace_net_get_params.argtypes = [_P, _F, ctypes.c_size_t]
+    L.lbm_ace_net_forward.argtypes = [_P, _P, _P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    L.lbm_ace_net_loss_grad.argtypes = [_P, _P, _P, _P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _F,
+                                        ctypes.c_size_t]
+    L.lbm_ace_net_adam.argtypes = [_P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float]
+    L.lbm_ace_net_gather.argtypes = [_P, _P, _P, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int, ctypes.c_longlong]
+    L.lbm_ace_net_metrics.argtypes = [_P, _P, ctypes.c_int, ctypes.c_int, _D, _D]
+    L.lbm_ace_net_synchronize.argtypes = [_P]
+    L.lbm_ace_net_last_error.argtypes = [_P]
+    L.lbm_ace_net_last_error.restype = ctypes.c_char_p
+    L.lbm_ace_net_destroy.argtypes = [_P]
+    L.lbm_ace_net_destroy.restype = None
+    L.lbm_ace_hybrid_advance.argtypes = [_P, _P, ctypes.c_longlong, ctypes.c_double, ctypes.c_double,
+                                         ctypes.POINTER(lbm_ace_hybrid_stats)]
+    for name in ("lbm_ace_net_create", "lbm_ace_net_set_params", "lbm_ace_net_get_params", "lbm_ace_net_forward",
+                 "lbm_ace_net_loss_grad", "lbm_ace_net_adam", "lbm_ace_net_gather", "lbm_ace_net_metrics",
+                 "lbm_ace_net_synchronize", "lbm_ace_hybrid_advance"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -267,6 +311,24 @@ class Lattice:
 
     synchronize = lbm_ace_synchronize
 
+    # -- device-side access (pointers are device addresses, e.g. tensor.data_ptr()) --
+    def lbm_ace_get_phi_device(self, phi_ptr: int) -> None:
+        _check(self.ctx, self._lib.lbm_ace_get_phi_device(self.ctx, _P(phi_ptr)))
+
+    def lbm_ace_velocity_device(self, t: float, u_ptr: int, v_ptr: int) -> None:
+        _check(self.ctx, self._lib.lbm_ace_velocity_device(self.ctx, float(t), _P(u_ptr), _P(v_ptr)))
+
+    def lbm_ace_reset_device(self, phi_ptr: int, t: int) -> None:
+        _check(self.ctx, self._lib.lbm_ace_reset_device(self.ctx, _P(phi_ptr), int(t)))
+
+    def lbm_ace_get_stream(self) -> int:
+        return int(self._lib.lbm_ace_get_stream(self.ctx) or 0)
+
+    def lbm_ace_get_params(self) -> lbm_ace_params:
+        p = lbm_ace_params()
+        _check(self.ctx, self._lib.lbm_ace_get_params(self.ctx, ctypes.byref(p)))
+        return p
+
     def close(self) -> None:
         if getattr(self, "ctx", None):
             self._lib.lbm_ace_destroy(self.ctx)
@@ -360,6 +422,115 @@ class Batch:
         if getattr(self, "h", None):
             self._lib.lbm_ace_batch_destroy(self.h)
             self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def _ptr(x) -> int:
+    """Device address of a torch tensor (data_ptr) or an int."""
+    return int(x.data_ptr()) if hasattr(x, "data_ptr") else int(x)
+
+
+class Net:
+    """The learned surrogate (wraps lbm_ace_net_create ... lbm_ace_net_destroy). Image
+    arguments are device FP32 arrays of [batch, ny, nx] given as torch tensors or
+    device addresses; all arithmetic runs in the library's kernels."""
+
+    def __init__(self, device: int = 0, stream=None):
+        self._lib = load()
+        h = _P()
+        s = 0 if stream is None else int(getattr(stream, "cuda_stream", stream))
+        rc = self._lib.lbm_ace_net_create(int(device), _P(s), ctypes.byref(h))
+        if rc != OK:
+            raise LbmAceError(rc, (self._lib.lbm_ace_net_last_error(None) or b"").decode(errors="replace"))
+        self.h = h
+
+    def _check(self, rc):
+        if rc != OK:
+            raise LbmAceError(rc, (self._lib.lbm_ace_net_last_error(self.h) or b"").decode(errors="replace"))
+
+    def lbm_ace_net_set_params(self, params) -> None:
+        a = np.ascontiguousarray(params, dtype=np.float32)
+        self._check(self._lib.lbm_ace_net_set_params(self.h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), a.size))
+
+    set_params = lbm_ace_net_set_params
+
+    def lbm_ace_net_get_params(self) -> np.ndarray:
+        a = np.empty(NET_PARAMS, dtype=np.float32)
+        self._check(self._lib.lbm_ace_net_get_params(self.h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), a.size))
+        return a
+
+    get_params = lbm_ace_net_get_params
+
+    def lbm_ace_net_forward(self, phi, u, v, phi_out, batch: int, ny: int, nx: int) -> None:
+        self._check(self._lib.lbm_ace_net_forward(self.h, _P(_ptr(phi)), _P(_ptr(u)), _P(_ptr(v)),
+                                                  _P(_ptr(phi_out)), int(batch), int(ny), int(nx)))
+
+    forward = lbm_ace_net_forward
+
+    def lbm_ace_net_loss_grad(self, phi, u, v, target, batch: int, ny: int, nx: int,
+                              want_loss: bool = True, want_grad: bool = False):
+        loss = ctypes.c_double(float("nan"))
+        g = np.empty(NET_PARAMS, dtype=np.float32) if want_grad else None
+        self._check(self._lib.lbm_ace_net_loss_grad(
+            self.h, _P(_ptr(phi)), _P(_ptr(u)), _P(_ptr(v)), _P(_ptr(target)), int(batch), int(ny), int(nx),
+            ctypes.byref(loss) if want_loss else None,
+            g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)) if want_grad else None, NET_PARAMS if want_grad else 0))
+        return (loss.value if want_loss else None), g
+
+    loss_grad = lbm_ace_net_loss_grad
+
+    def lbm_ace_net_adam(self, lr: float, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8) -> None:
+        self._check(self._lib.lbm_ace_net_adam(self.h, lr, beta1, beta2, eps))
+
+    adam = lbm_ace_net_adam
+
+    def lbm_ace_net_gather(self, dst, src, index, image_elems: int) -> None:
+        idx = np.ascontiguousarray(index, dtype=np.int64)
+        self._check(self._lib.lbm_ace_net_gather(self.h, _P(_ptr(dst)), _P(_ptr(src)),
+                                                 idx.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)), idx.size,
+                                                 int(image_elems)))
+
+    gather = lbm_ace_net_gather
+
+    def lbm_ace_net_metrics(self, phi, ny: int, nx: int):
+        m, w = ctypes.c_double(), ctypes.c_double()
+        self._check(self._lib.lbm_ace_net_metrics(self.h, _P(_ptr(phi)), int(ny), int(nx), ctypes.byref(m),
+                                                  ctypes.byref(w)))
+        return m.value, w.value
+
+    metrics = lbm_ace_net_metrics
+
+    def lbm_ace_net_synchronize(self) -> None:
+        self._check(self._lib.lbm_ace_net_synchronize(self.h))
+
+    synchronize = lbm_ace_net_synchronize
+
+    def lbm_ace_hybrid_advance(self, lattice: "Lattice", windows: int, mass_tol: float = 1e-6,
+                               width_tol: float = 0.1) -> dict:
+        st = lbm_ace_hybrid_stats()
+        self._check(self._lib.lbm_ace_hybrid_advance(lattice.ctx, self.h, int(windows), float(mass_tol),
+                                                     float(width_tol), ctypes.byref(st)))
+        return {f: getattr(st, f) for f, _ in lbm_ace_hybrid_stats._fields_}
+
+    hybrid_advance = lbm_ace_hybrid_advance
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            self._lib.lbm_ace_net_destroy(self.h)
+            self.h = None
+
+    lbm_ace_net_destroy = close
 
     def __del__(self):
         try:

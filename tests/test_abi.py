@@ -103,3 +103,37 @@ def test_consistent_mobility_is_accepted_by_validation():
         A.Lattice(nx=8, ny=8, tau=0.8, M=0.1)
     except A.LbmAceError as e:
         assert e.status in (A.ECUDA, A.ENOMEM), e
+
+
+def test_hybrid_stats_layout_matches_header(tmp_path):
+    fields = [f for f, _ in A.lbm_ace_hybrid_stats._fields_]
+    src = ['#include <stdio.h>', '#include <stddef.h>', '#include "lbm_ace_surrogate.h"', "int main(void){",
+           'printf("%zu\\n", sizeof(lbm_ace_hybrid_stats));',
+           'printf("%d %d %d\\n", LBM_ACE_NET_WIDTH, LBM_ACE_NET_K, LBM_ACE_NET_PARAMS);']
+    for f in fields:
+        src.append(f'printf("%zu\\n", offsetof(lbm_ace_hybrid_stats, {f}));')
+    src.append("return 0;}")
+    c = tmp_path / "layout.c"
+    c.write_text("\n".join(src))
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(c), "-o", str(exe)], check=True)
+    vals = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    assert vals[0] == ctypes.sizeof(A.lbm_ace_hybrid_stats)
+    assert vals[1:4] == [A.NET_WIDTH, A.NET_K, A.NET_PARAMS]
+    for f, off in zip(fields, vals[4:]):
+        assert getattr(A.lbm_ace_hybrid_stats, f).offset == off, f
+
+
+def test_net_parameter_count_matches_the_oracle():
+    from oracle import surrogate as S
+    assert S.param_count() == A.NET_PARAMS
+    assert S.K_STEPS == A.NET_K and S.WIDTHS[1] == A.NET_WIDTH
+
+
+def test_net_entry_points_reject_null_handles():
+    L = A.load()
+    assert L.lbm_ace_net_set_params(None, None, 0) == A.EINVAL
+    assert L.lbm_ace_net_forward(None, None, None, None, None, 1, 8, 8) == A.EINVAL
+    assert L.lbm_ace_hybrid_advance(None, None, 1, 1e-6, 0.1, None) == A.EINVAL
+    assert L.lbm_ace_get_phi_device(None, None) == A.EINVAL
+    assert b"NULL" in L.lbm_ace_net_last_error(None)

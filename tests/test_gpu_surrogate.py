@@ -1,0 +1,225 @@
+"""GPU parity of the learned surrogate's kernels against the FP64 oracle, the
+device-side lattice helpers, and the hybrid advance's fallback logic (through the C ABI).
+
+Tolerances. The oracle's ``emulate`` mode rounds to BF16 exactly where the kernels store
+BF16 (weights of layers 2-4, z_l and a_l of layers 1-4, dL/dz_l), so the two sides
+differ only by accumulation order (FP32 in the kernels, FP64 in the oracle), erff vs the
+FP64 erf, and the rare BF16 rounding that the two land on opposite sides of (a 2^-8
+relative change of one stored value). For 288-term dot products the FP32 error is
+~1e-6 of the terms, so a flip happens for ~5e-4 of the stored values; four layers of
+such flips move the result by ~2e-4 relative (L2), hence 2e-3 for the forward increment
+and 1e-2 for the gradients (whose last reduction runs over all pixels). Against the
+pure FP64 oracle the BF16 storage itself shows; 5e-2 bounds it.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import surrogate as S
+from paper_2203_05230_gb300 import lbm_ace as A
+from paper_2203_05230_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-300))
+
+
+def dev(a):
+    return torch.tensor(np.asarray(a, dtype=np.float32), device="cuda")
+
+
+def problem(B, H, Wd, seed, scale_out=20.0):
+    rng = np.random.default_rng(seed)
+    flat = W.surrogate_init_params(seed=seed)
+    flat[-289:] *= scale_out                 # a visible increment from the output layer
+    flat[:896] += rng.standard_normal(896) * 0.05
+    phi = np.stack([W.circles_phi0(max(H, Wd), np.random.Generator(np.random.PCG64(seed + b)))[:H, :Wd]
+                    for b in range(B)])
+    u = rng.uniform(-0.05, 0.05, (B, H, Wd))
+    v = rng.uniform(-0.05, 0.05, (B, H, Wd))
+    tgt = phi + rng.standard_normal((B, H, Wd)) * 0.02
+    f32 = lambda a: np.asarray(a, dtype=np.float32).astype(np.float64)
+    return f32(flat), f32(phi), f32(u), f32(v), f32(tgt)
+
+
+SHAPES = [(1, 16, 16), (2, 40, 48), (1, 5, 7), (3, 33, 17), (1, 64, 64)]
+
+
+@pytest.fixture(scope="module")
+def net():
+    n = A.Net(device=0, stream=torch.cuda.current_stream())
+    yield n
+    n.close()
+
+
+@pytest.mark.parametrize("B,H,Wd", SHAPES)
+def test_forward_matches_oracle(net, B, H, Wd):
+    flat, phi, u, v, _ = problem(B, H, Wd, seed=B * 100 + H)
+    net.set_params(flat)
+    out = torch.empty((B, H, Wd), dtype=torch.float32, device="cuda")
+    net.forward(dev(phi), dev(u), dev(v), out, B, H, Wd)
+    got = out.cpu().numpy().astype(np.float64)
+    emu, _ = S.forward(flat, phi, u, v, emulate=True)
+    exact, _ = S.forward(flat, phi, u, v)
+    assert rel(got - phi, emu - phi) < 2e-3
+    assert rel(got - phi, exact - phi) < 5e-2
+    assert np.allclose(got.sum(axis=(1, 2)), phi.sum(axis=(1, 2)), rtol=2e-6, atol=1e-4)
+
+
+@pytest.mark.parametrize("B,H,Wd", SHAPES)
+def test_gradient_matches_oracle(net, B, H, Wd):
+    flat, phi, u, v, tgt = problem(B, H, Wd, seed=7 + B * 10 + Wd)
+    net.set_params(flat)
+    loss, g = net.loss_grad(dev(phi), dev(u), dev(v), dev(tgt), B, H, Wd, want_loss=True, want_grad=True)
+    Le, ge, _ = S.loss_and_grad(flat, phi, u, v, tgt, emulate=True)
+    Lx, gx, _ = S.loss_and_grad(flat, phi, u, v, tgt)
+    assert abs(loss - Le) < 1e-3 * Le
+    k = 0
+    gn = np.linalg.norm(ge)
+    for shp in S.param_shapes():
+        n = int(np.prod(shp))
+        # b_5 has an identically zero gradient (the mean removal absorbs it): absolute part
+        d = np.linalg.norm(g[k:k + n] - ge[k:k + n])
+        assert d < 1e-2 * np.linalg.norm(ge[k:k + n]) + 1e-6 * gn, (shp, k)
+        k += n
+    assert rel(g, ge) < 5e-3
+    assert rel(g, gx) < 5e-2
+
+
+def test_adam_matches_oracle(net):
+    flat, phi, u, v, tgt = problem(2, 32, 32, seed=11)
+    net.set_params(flat)
+    _, g = net.loss_grad(dev(phi), dev(u), dev(v), dev(tgt), 2, 32, 32, want_loss=False, want_grad=True)
+    net.adam(1e-3, 0.9, 0.999, 1e-8)
+    p1 = net.get_params().astype(np.float64)
+    ref, m, vv = S.adam(flat, g.astype(np.float64), np.zeros_like(flat), np.zeros_like(flat), 1, 1e-3)
+    assert np.abs(p1 - ref).max() < 1e-6 * max(1.0, np.abs(ref).max())
+    _, g2 = net.loss_grad(dev(phi), dev(u), dev(v), dev(tgt), 2, 32, 32, want_loss=False, want_grad=True)
+    net.adam(1e-3, 0.9, 0.999, 1e-8)
+    p2 = net.get_params().astype(np.float64)
+    ref2, _, _ = S.adam(p1, g2.astype(np.float64), m, vv, 2, 1e-3)
+    assert np.abs(p2 - ref2).max() < 1e-6 * max(1.0, np.abs(ref2).max())
+
+
+def test_metrics_match_oracle(net):
+    phi = W.disk_phi0(96, 80, 40.0, 50.0, 20.0, 1.0).astype(np.float32)
+    m, w = net.metrics(dev(phi), 80, 96)
+    p64 = phi.astype(np.float64)
+    assert abs(m - S.mass(p64)) < 1e-12 * S.mass(p64)
+    assert abs(w - S.interface_width(p64)) < 1e-9
+
+
+def test_gather_copies_images(net):
+    src = torch.arange(5 * 12, dtype=torch.float32, device="cuda").reshape(5, 3, 4)
+    dst = torch.empty((3, 3, 4), dtype=torch.float32, device="cuda")
+    net.gather(dst, src, [4, 0, 2], 12)
+    net.synchronize()
+    assert torch.equal(dst, src[[4, 0, 2]])
+
+
+def test_zero_network_is_the_identity(net):
+    net.set_params(np.zeros(A.NET_PARAMS))
+    phi = np.random.default_rng(3).uniform(0, 1, (2, 24, 40)).astype(np.float32)
+    out = torch.empty((2, 24, 40), dtype=torch.float32, device="cuda")
+    z = torch.zeros((2, 24, 40), dtype=torch.float32, device="cuda")
+    net.forward(dev(phi), z, z, out, 2, 24, 40)
+    assert np.array_equal(out.cpu().numpy(), phi)
+
+
+# --- device-side lattice helpers -------------------------------------------------
+
+def test_phi_and_velocity_on_the_device():
+    L = 48
+    with A.vortex_lattice(L, T=512, precision=A.F32) as g:
+        g.step(7)
+        phi = torch.empty((L, L), dtype=torch.float32, device="cuda")
+        u = torch.empty_like(phi)
+        v = torch.empty_like(phi)
+        g.lbm_ace_get_phi_device(phi.data_ptr())
+        g.lbm_ace_velocity_device(100.0, u.data_ptr(), v.data_ptr())
+        g.synchronize()
+        assert np.array_equal(phi.cpu().numpy(), g.phi().astype(np.float32))
+        y, x = np.mgrid[0:L, 0:L].astype(np.float64)
+        c = math.cos(math.pi * 100.0 / 512)
+        ue = -0.04 * np.sin(math.pi * x / L) ** 2 * np.sin(2 * math.pi * y / L) * c
+        ve = 0.04 * np.sin(math.pi * y / L) ** 2 * np.sin(2 * math.pi * x / L) * c
+        assert np.abs(u.cpu().numpy() - ue).max() < 2e-8 and np.abs(v.cpu().numpy() - ve).max() < 2e-8
+
+
+def test_reset_at_zero_equals_a_fresh_lattice():
+    L = 40
+    phi0 = W.disk_phi0(L, L, 20.0, 24.0, 9.0, 1.0).astype(np.float32)
+    with A.vortex_lattice(L, T=400, precision=A.F32) as g, \
+         A.vortex_lattice(L, T=400, precision=A.F32, phi0=phi0.astype(np.float64)) as h:
+        g.step(13)
+        g.lbm_ace_reset_device(dev(phi0).data_ptr(), 0)
+        g.synchronize()
+        assert g.t == 0
+        g.step(25)
+        h.step(25)
+        assert np.array_equal(g.phi(), h.phi())
+
+
+@pytest.mark.parametrize("prec,tol_phi,tol_mass", [(A.F64, 1e-12, 1e-12), (A.F32, 2e-6, 1e-5),
+                                                    (A.BF16DEV, 2e-4, 1e-4)])
+def test_reset_keeps_phi_and_time(prec, tol_phi, tol_mass):
+    # 16-bit storage: the deviations f_i - s_i phi (up to ~0.013 under the vortex) round to
+    # 2^-9 of themselves, a few 1e-5 in phi
+    L = 32
+    phi = W.disk_phi0(L, L, 16.0, 16.0, 8.0, 1.0).astype(np.float32)
+    with A.vortex_lattice(L, T=320, precision=prec) as g:
+        g.lbm_ace_reset_device(dev(phi).data_ptr(), 77)
+        g.synchronize()
+        assert g.t == 77
+        assert np.abs(g.phi() - phi).max() < tol_phi
+        m0 = g.mass()
+        g.step(32)
+        assert abs(g.mass() - m0) < tol_mass * m0
+
+
+# --- hybrid advance ----------------------------------------------------------------
+
+def field_lattice(L, seed, stream):
+    phi0, u, v = W.surrogate_trajectories(1, L, seed)[0]
+    return A.Lattice(nx=L, ny=L, tau=0.8, eps=1.0, precision=A.F32, velocity_kind=A.VEL_FIELD,
+                     u_field=u, v_field=v, phi0=phi0, stream=stream)
+
+
+def test_hybrid_with_rejected_windows_is_the_plain_lattice(net):
+    s = torch.cuda.current_stream()
+    flat = W.surrogate_init_params(seed=5)
+    flat[-289:] *= 200.0  # an untrained network that changes the interface width
+    net.set_params(flat)
+    with field_lattice(64, 1, s) as a, field_lattice(64, 1, s) as b:
+        st = net.hybrid_advance(a, 6, mass_tol=1e-6, width_tol=1e-3)
+        b.step(6 * A.NET_K)
+        assert st["fallback_windows"] == 6 and st["surrogate_windows"] == 0
+        assert a.t == b.t == 96
+        assert np.array_equal(a.phi(), b.phi())
+
+
+def test_hybrid_with_accepted_windows_moves_time_and_keeps_mass(net):
+    s = torch.cuda.current_stream()
+    net.set_params(np.zeros(A.NET_PARAMS))  # identity network: always accepted
+    with field_lattice(64, 2, s) as a:
+        phi0 = a.phi()
+        m0 = a.mass()
+        st = net.hybrid_advance(a, 5, mass_tol=1e-6, width_tol=0.1)
+        assert st["surrogate_windows"] == 5 and st["fallback_windows"] == 0
+        assert a.t == 5 * A.NET_K
+        assert np.abs(a.phi() - phi0).max() < 2e-6
+        assert abs(a.mass() - m0) < 1e-6 * m0
+        a.step(16)  # the lattice continues from the restarted state
+        assert abs(a.mass() - m0) < 1e-5 * m0
+
+
+def test_hybrid_rejects_a_lattice_on_another_stream(net):
+    other = torch.cuda.Stream()
+    with field_lattice(32, 3, other) as a:
+        with pytest.raises(A.LbmAceError) as e:
+            net.hybrid_advance(a, 1)
+        assert e.value.status == A.EINVAL
