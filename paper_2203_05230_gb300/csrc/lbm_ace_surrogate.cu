@@ -76,10 +76,23 @@ __host__ __device__ inline Geo make_geo(int B, int H, int W)
     return g;
 }
 
-__device__ __forceinline__ int wrapi(int v, int n)
+// v in [-1, 2n): one conditional add or subtract (a neighbour of a node inside the image)
+__device__ __forceinline__ int wrap1(int v, int n)
 {
-    v %= n;
-    return v < 0 ? v + n : v;
+    v = v < 0 ? v + n : v;
+    return v >= n ? v - n : v;
+}
+
+// v >= -1 (a halo row or column of a tile that starts inside the image); images narrower
+// than a tile can wrap more than once
+__device__ __forceinline__ int wrap_halo(int v, int n)
+{
+    if (v < 0) v += n;
+    if (v >= n) {
+        v -= n;
+        if (v >= n) v %= n;
+    }
+    return v;
 }
 
 __device__ __forceinline__ void tile_origin(const Geo& g, long long t, int& b, int& y0, int& x0)
@@ -150,7 +163,7 @@ __device__ __forceinline__ void load_halo(bf16* hs, const bf16* __restrict__ in,
     for (int k = tid; k < HPX * 4; k += nthreads) {
         const int q = k >> 2, part = k & 3;
         const int hy = q / HWD, hx = q - hy * HWD;
-        const int y = wrapi(y0 + hy - 1, g.H), x = wrapi(x0 + hx - 1, g.W);
+        const int y = wrap_halo(y0 + hy - 1, g.H), x = wrap_halo(x0 + hx - 1, g.W);
         const bf16* src = in + ((((size_t)b * g.H + y) * g.W + x) * C + part * 8);
         cp_async16(hs + q * PS + part * 8, src);
     }
@@ -174,10 +187,10 @@ __global__ void __launch_bounds__(256) surr_in_fwd(const float* __restrict__ phi
         float in[27];
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
-            const int yy = wrapi(y + j - 1, H);
+            const int yy = wrap1(y + j - 1, H);
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
-                const long long q = (b * H + yy) * W + wrapi(x + i - 1, W);
+                const long long q = (b * H + yy) * W + wrap1(x + i - 1, W);
                 in[j * 3 + i] = phi[q];
                 in[9 + j * 3 + i] = u[q] * U_SCALE;
                 in[18 + j * 3 + i] = v[q] * U_SCALE;
@@ -215,7 +228,7 @@ __global__ void __launch_bounds__(256) surr_in_fwd(const float* __restrict__ phi
 enum { MODE_FWD = 0, MODE_DGRAD = 1 };
 
 template <int MODE>
-__global__ void __launch_bounds__(CONV_THREADS) surr_conv_mma(const bf16* __restrict__ in, const bf16* __restrict__ wpk,
+__global__ void __launch_bounds__(CONV_THREADS, 3) surr_conv_mma(const bf16* __restrict__ in, const bf16* __restrict__ wpk,
                                                               const float* __restrict__ bias,
                                                               const bf16* __restrict__ zaux, bf16* __restrict__ out_z,
                                                               bf16* __restrict__ out_a, const Geo g)
@@ -263,25 +276,25 @@ __global__ void __launch_bounds__(CONV_THREADS) surr_conv_mma(const bf16* __rest
                 for (int e = 0; e < 4; ++e) acc[mt][nt][e] = 0.0f;
 
         const int r0 = warp * 2;
-#pragma unroll 1
+        // per-lane ldmatrix row addresses at tap (0, 0), k-half 0; every (tap, k-half)
+        // adds a compile-time byte offset
+        const unsigned a_addr = hs_base + (unsigned)(((r0 * HWD + (lq & 1) * 8 + lr) * PS + (lq >> 1) * 8) * 2);
+        const unsigned b_addr = ws_base + (unsigned)((((lq >> 1) * 8 + lr) * PS + (lq & 1) * 8) * 2);
+#pragma unroll
         for (int tap = 0; tap < 9; ++tap) {
-            const int j = tap / 3, i = tap - 3 * (tap / 3);
+            const int j = tap / 3, i = tap % 3;
 #pragma unroll
             for (int kh = 0; kh < 2; ++kh) {
                 unsigned a[2][4];
 #pragma unroll
-                for (int mt = 0; mt < 2; ++mt) {
-                    const int px = (r0 + mt + j) * HWD + i + (lq & 1) * 8 + lr;
-                    ldsm_x4(hs_base + (unsigned)(px * PS + kh * 16 + (lq >> 1) * 8) * 2u, a[mt][0], a[mt][1], a[mt][2],
+                for (int mt = 0; mt < 2; ++mt)
+                    ldsm_x4(a_addr + (unsigned)((((mt + j) * HWD + i) * PS + kh * 16) * 2), a[mt][0], a[mt][1], a[mt][2],
                             a[mt][3]);
-                }
                 unsigned bfr[4][2];
 #pragma unroll
-                for (int nb = 0; nb < 2; ++nb) {
-                    const int row = tap * C + nb * 16 + (lq >> 1) * 8 + lr;
-                    ldsm_x4(ws_base + (unsigned)(row * PS + kh * 16 + (lq & 1) * 8) * 2u, bfr[2 * nb][0],
+                for (int nb = 0; nb < 2; ++nb)
+                    ldsm_x4(b_addr + (unsigned)(((tap * C + nb * 16) * PS + kh * 16) * 2), bfr[2 * nb][0],
                             bfr[2 * nb][1], bfr[2 * nb + 1][0], bfr[2 * nb + 1][1]);
-                }
 #pragma unroll
                 for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
@@ -448,7 +461,7 @@ __global__ void __launch_bounds__(256) surr_out_fwd(const bf16* __restrict__ a4,
         float acc = w[288];
 #pragma unroll 1
         for (int tap = 0; tap < 9; ++tap) {
-            const int yy = wrapi(y + tap / 3 - 1, H), xx = wrapi(x + tap % 3 - 1, W);
+            const int yy = wrap1(y + tap / 3 - 1, H), xx = wrap1(x + tap % 3 - 1, W);
             const uint4* src = reinterpret_cast<const uint4*>(a4 + (((size_t)b * H + yy) * W + xx) * C);
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
@@ -556,7 +569,7 @@ __global__ void __launch_bounds__(256) surr_out_bwd(const bf16* __restrict__ a4,
         cp_commit();
         for (int q = tid; q < HPX; q += 256) {
             const int hy = q / HWD, hx = q - hy * HWD;
-            const int y = wrapi(y0 + hy - 1, g.H), x = wrapi(x0 + hx - 1, g.W);
+            const int y = wrap_halo(y0 + hy - 1, g.H), x = wrap_halo(x0 + hx - 1, g.W);
             gh[q] = gz5[((size_t)b * g.H + y) * g.W + x];
         }
         cp_wait<0>();
@@ -653,7 +666,7 @@ __global__ void __launch_bounds__(256) surr_in_wgrad(const bf16* __restrict__ gz
         }
         for (int q = tid; q < HPX; q += 256) {
             const int hy = q / HWD, hx = q - hy * HWD;
-            const int y = wrapi(y0 + hy - 1, g.H), x = wrapi(x0 + hx - 1, g.W);
+            const int y = wrap_halo(y0 + hy - 1, g.H), x = wrap_halo(x0 + hx - 1, g.W);
             const size_t k = ((size_t)b * g.H + y) * g.W + x;
             xs[0][q] = phi[k];
             xs[1][q] = u[k] * U_SCALE;
@@ -736,8 +749,8 @@ __global__ void __launch_bounds__(256) surr_metrics(const float* __restrict__ ph
         const double f = phi[q];
         sm += f;
         if (f > 0.05 && f < 0.95) {
-            const double gx = 0.5 * ((double)phi[(long long)y * W + wrapi(x + 1, W)] - (double)phi[(long long)y * W + wrapi(x - 1, W)]);
-            const double gy = 0.5 * ((double)phi[(long long)wrapi(y + 1, H) * W + x] - (double)phi[(long long)wrapi(y - 1, H) * W + x]);
+            const double gx = 0.5 * ((double)phi[(long long)y * W + wrap1(x + 1, W)] - (double)phi[(long long)y * W + wrap1(x - 1, W)]);
+            const double gy = 0.5 * ((double)phi[(long long)wrap1(y + 1, H) * W + x] - (double)phi[(long long)wrap1(y - 1, H) * W + x]);
             sp += f * (1.0 - f);
             sgr += sqrt(gx * gx + gy * gy);
         }

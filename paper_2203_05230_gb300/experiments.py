@@ -15,8 +15,12 @@ the results (phi-L1/L2 against a reference field, mass drift, interface width).
 
 * ``batch_study``: 256 lattices of uneven size in one persistent, graph-replayed
   launch per step (tiles from the autotuner) against one launch per lattice per step.
+* ``surrogate_study``: the learned surrogate of 16 steps trained on 20,000 pairs that the
+  GPU solver generates (625 trajectories x 32 windows on 256^2 tiles), evaluated on
+  held-out trajectories against persistence, then rolled out over one period of the
+  256^2 vortex with the lattice Boltzmann fallback, against the plain FP32 run.
 
-Run: python -m paper_2203_05230_gb300.experiments {ablation,fp32,precision,batch} (one GPU).
+Run: python -m paper_2203_05230_gb300.experiments {ablation,fp32,precision,batch,surrogate} (one GPU).
 The paper's eps is 4x the eps used here (psi = eps ln(phi / (1 - phi)) as printed
 in Eq. 13); tables give both.
 """
@@ -157,10 +161,48 @@ def batch_study(count=256, steps=20, tune_steps=3):
             "speedup": dt_s / dt_g}
 
 
+def surrogate_study(n_traj=625, pairs=32, steps=6000, batch=16, held_out=25, L=256, seed=0, lr_max=2e-3,
+                    save_params=None):
+    """Train the surrogate on trajectories 0 .. n_traj - held_out - 1 and report held-out
+    errors, the untrained network's error, training throughput and the vortex rollout;
+    the trained parameters go to the .npy file `save_params` if given."""
+    import torch
+    from . import surrogate as SG
+    s = torch.cuda.current_stream()
+    out = {"study": f"surrogate: {n_traj} trajectories x {pairs} windows of {SG.K} steps on {L}^2 "
+                    f"(held out {held_out}), {steps} Adam steps of batch {batch}"}
+    t0 = time.perf_counter()
+    data = SG.generate(n_traj, pairs, L=L, seed=seed, stream=s)
+    torch.cuda.synchronize()
+    out["generate_seconds"] = time.perf_counter() - t0
+    out["pairs"] = data.n_pairs
+    n_train = (n_traj - held_out) * pairs
+    train_idx, test_idx = np.arange(n_train), np.arange(n_train, data.n_pairs)
+    with A.Net(0, s) as net:
+        net.set_params(W.surrogate_init_params(seed=seed))
+        tr = SG.Trainer(net, data, batch=batch, seed=seed)
+        out["untrained"] = tr.evaluate(test_idx)
+        t0 = time.perf_counter()
+        hist = tr.train(steps, lr_max=lr_max, train_pairs=train_idx, log_every=max(1, steps // 20))
+        out["train_seconds"] = time.perf_counter() - t0
+        out["train_pairs_per_second"] = steps * batch / out["train_seconds"]
+        out["loss_history"] = hist
+        out["held_out"] = tr.evaluate(test_idx)
+        out["train_subset"] = tr.evaluate(train_idx[:len(test_idx)])
+        out["rollout_256"] = SG.vortex_rollout(net, L=256, stream=s)
+        out["params_sha16"] = __import__("hashlib").sha256(net.get_params().tobytes()).hexdigest()[:16]
+        if save_params:
+            np.save(save_params, net.get_params())
+    return out
+
+
 def main(argv):
     which = argv[1] if len(argv) > 1 else "ablation"
-    res = {"ablation": paper_ablation, "fp32": fp32_study, "precision": precision_study,
-           "batch": batch_study}[which]()
+    if which == "surrogate":
+        res = surrogate_study(save_params=argv[2] if len(argv) > 2 else None)
+    else:
+        res = {"ablation": paper_ablation, "fp32": fp32_study, "precision": precision_study,
+               "batch": batch_study}[which]()
     print(json.dumps(res))
 
 
