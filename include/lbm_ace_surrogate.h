@@ -16,11 +16,14 @@
  * z Phi(z) with Phi the standard normal CDF. Removing the mean of z_5 conserves
  * sum(phi), the global mass that Eq. 8's divergence form conserves.
  *
- * Arithmetic: layers 2-4 (96 % of the multiply-adds) run on the tensor cores with
- * BF16 weights and activations and FP32 accumulation; layers 1 and 5 run on the
- * FP32 units with FP32 weights; stored activations z_l, a_l and back-propagated
- * gradients dL/dz_l of layers 1-4 are BF16; phi, u, v, phi_out, the loss and the
- * weight gradients are FP32 (gradient sums over pixels in FP64 across CTAs).
+ * Arithmetic: layers 2-5 (97 % of the multiply-adds) and the input gradients of
+ * layers 2-4 run on the fifth-generation tensor cores (tcgen05.mma, BF16 weights and
+ * activations, FP32 accumulation in tensor memory); the weight gradients of layers
+ * 2-4 on the tensor cores through mma.sync; layer 1 (3 input channels) and the layer-5
+ * and layer-1 gradients on the FP32 units (layer 1 with FP32 weights). Stored
+ * activations z_l, a_l and back-propagated gradients dL/dz_l of layers 1-4 are BF16;
+ * phi, u, v, phi_out, z_5, the loss and the weight gradients are FP32 (gradient sums
+ * over pixels in FP64 across CTAs).
  *
  * Conventions (as in lbm_ace.h): every function returns a status (LBM_ACE_OK = 0,
  * negative on error, codes of lbm_ace.h) and never aborts; messages through
@@ -92,6 +95,12 @@ int lbm_ace_net_metrics(lbm_ace_net* net, const float* phi, int ny, int nx, doub
 /* Block until the net's device work has finished. */
 int lbm_ace_net_synchronize(lbm_ace_net* net);
 
+/* Launch shape of the persistent tensor-core kernels: CTAs launched (at most) for the
+ * hidden layers and for layer 5, the resident CTAs per SM the occupancy calculator
+ * reports for each, and the SM count. Any pointer may be NULL. */
+int lbm_ace_net_launch_shape(const lbm_ace_net* net, int* conv_ctas, int* conv_occupancy, int* out_ctas,
+                             int* out_occupancy, int* sms);
+
 const char* lbm_ace_net_last_error(const lbm_ace_net* net);
 
 /* Release all device memory (NULL-safe). */
@@ -106,8 +115,11 @@ void lbm_ace_net_destroy(lbm_ace_net* net);
  * lattice Boltzmann steps instead, restarting the lattice from the current phi
  * (lbm_ace_reset_device) when surrogate windows came before. On return the lattice
  * holds phi at t0 + K * windows (restarted from the surrogate's field if the last
- * window was a surrogate window). The lattice must be an FP32 single-lattice context
- * with a vortex, uniform or field velocity, working on the same stream as the net.
+ * window was a surrogate window). The lattice may have any storage precision and a
+ * vortex, uniform or field velocity; it must work on the same stream as the net.
+ * Up to 8 surrogate windows run back to back on the device before the host reads
+ * their checks (one synchronisation per group); the windows after a rejected one are
+ * discarded, so the result is the same as checking window by window.
  * stats (may be NULL) receives the counts and the extreme deviations accepted. */
 typedef struct {
     long long windows;           /* windows advanced */

@@ -30,11 +30,11 @@ Parameters travel as one flat vector in the order W_1, b_1, ..., W_5, b_5, each 
 interchange format of the C library's ``lbm_ace_net_set_params``.
 
 ``emulate=True`` rounds to BF16 (round to nearest even, through FP32) exactly where the
-CUDA path stores BF16: the weights of layers 2-4, the stored z_l and a_l of layers 1-4
-and the back-propagated dL/dz_l of layers 1-4. Layers 1 and 5, which the CUDA path
-runs on FP32 units, keep FP32 weights. This makes the comparison with the GPU a test
-of the arithmetic, not of the storage precision; the pure FP64 mode gives the
-storage error.
+CUDA path stores BF16: the weights of layers 2-5 (tensor-core operands), the stored z_l
+and a_l of layers 1-4 and the back-propagated dL/dz_l of layers 1-4. Layer 1, which the
+CUDA path runs on FP32 units, keeps FP32 weights. This makes the comparison with the
+GPU a test of the arithmetic, not of the storage precision; the pure FP64 mode gives
+the storage error.
 """
 from __future__ import annotations
 
@@ -160,10 +160,9 @@ def _weights(flat, widths, emulate):
     layers = unpack(flat, widths)
     if not emulate:
         return layers
-    n = len(layers)
     out = []
     for l, (W, b) in enumerate(layers):
-        rw = f32 if l in (0, n - 1) else bf16
+        rw = f32 if l == 0 else bf16
         out.append((rw(W), f32(b)))
     return out
 

@@ -6,13 +6,13 @@
 //
 // Kernels (all hand-written):
 //   surr_in_fwd      layer 1 on FP32 units: 27 inputs -> 32 outputs per node
-//   surr_conv_mma    layers 2-4 forward and their input gradients: implicit GEMM on the
-//                    tensor cores (mma.sync m16n8k16, BF16 operands, FP32 accumulators),
-//                    16 x 16 output tiles, 18 x 18 x 32 halo staged by cp.async,
-//                    double-buffered, persistent CTAs
+//   surr_conv_umma   layers 2-5 forward and the input gradients of layers 2-4: implicit
+//                    GEMM on the fifth-generation tensor cores (tcgen05.mma, BF16
+//                    operands from shared memory, FP32 accumulators in tensor memory),
+//                    4 x 128 output tiles, persistent CTAs
 //   surr_wgrad_mma   layers 2-4 weight gradients: per-tap GEMM over the pixels on the
-//                    tensor cores (ldmatrix.trans operands), per-CTA partials
-//   surr_out_fwd / surr_residual   layer 5, mean removal, residual add
+//                    tensor cores (mma.sync m16n8k16, ldmatrix.trans operands), per-CTA partials
+//   surr_residual    mean removal of z_5 and the residual add
 //   surr_loss_part / surr_gz5      loss and dL/dz_5 through the mean removal
 //   surr_out_bwd     layer 5 weight gradient and dL/dz_4
 //   surr_in_wgrad    layer 1 weight gradient
@@ -52,10 +52,8 @@ constexpr int L1_N = 896;             // W1 (864) + b1 (32)
 constexpr int LH_N = 9248;            // W (9216) + b (32) of a hidden layer
 constexpr int L5_N = 289;             // W5 (288) + b5 (1)
 constexpr float U_SCALE = 20.0f;      // velocity input scale (1 / 0.05)
-constexpr int CONV_THREADS = 256;
 constexpr int WG_THREADS = 288;       // 9 warps, one per tap
 constexpr int RED_BLOCKS = 64;        // blocks per image for per-image reductions
-constexpr int W_SMEM = 9 * C * PS;    // packed weights of one layer in shared memory (bf16)
 
 static_assert(OFF_W2 == OFF_W1 + L1_N && OFF_W3 == OFF_W2 + LH_N && OFF_W4 == OFF_W3 + LH_N &&
               OFF_W5 == OFF_W4 + LH_N && OFF_W5 + L5_N == NPARAM, "parameter layout");
@@ -104,11 +102,71 @@ __device__ __forceinline__ void tile_origin(const Geo& g, long long t, int& b, i
     x0 = (r % g.tx) * TW;
 }
 
-__device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+// erfc(x) by the Chebyshev-fitted form of Numerical Recipes (Press et al., 2nd ed.,
+// Section 6.2): erfc(x) = t exp(-x^2 + P(t)), t = 1 / (1 + |x| / 2), P of degree 9, for
+// x >= 0 (fractional error below 1.2e-7 in exact arithmetic, ~1e-7 in FP32 where GELU
+// needs it), and 2 - erfc(-x) for x < 0. One reciprocal, one exponential, nine FMAs.
+__device__ __forceinline__ float erfc_nr(float x)
+{
+    const float ax = fabsf(x);
+    const float t = __fdividef(1.0f, fmaf(0.5f, ax, 1.0f));
+    float p = 0.17087277f;
+    p = fmaf(p, t, -0.82215223f);
+    p = fmaf(p, t, 1.48851587f);
+    p = fmaf(p, t, -1.13520398f);
+    p = fmaf(p, t, 0.27886807f);
+    p = fmaf(p, t, -0.18628806f);
+    p = fmaf(p, t, 0.09678418f);
+    p = fmaf(p, t, 0.37409196f);
+    p = fmaf(p, t, 1.00002368f);
+    p = fmaf(p, t, -1.26551223f);
+    const float y = t * __expf(fmaf(-ax, ax, p));
+    return x >= 0.0f ? y : 2.0f - y;
+}
+
+// GELU(z) = z Phi(z) = z erfc(-z / sqrt 2) / 2, and its derivative Phi(z) + z phi(z).
+__device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * erfc_nr(-0.70710678118654752f * z); }
 
 __device__ __forceinline__ float gelu_grad_f(float z)
 {
-    return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
+    return fmaf(z * 0.39894228040143268f, __expf(-0.5f * z * z), 0.5f * erfc_nr(-0.70710678118654752f * z));
+}
+
+// The same functions on two values at once with the packed FP32x2 instructions of
+// sm_100+ (each lane rounds as the scalar operation does, so the results are
+// bit-identical to gelu_f / gelu_grad_f).
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+
+__device__ __forceinline__ float2 erfc_nr2(float2 x)
+{
+    const float2 ax = make_float2(fabsf(x.x), fabsf(x.y));
+    const float2 d = __ffma2_rn(f2(0.5f), ax, f2(1.0f));
+    const float2 t = make_float2(__fdividef(1.0f, d.x), __fdividef(1.0f, d.y));
+    float2 p = f2(0.17087277f);
+    p = __ffma2_rn(p, t, f2(-0.82215223f));
+    p = __ffma2_rn(p, t, f2(1.48851587f));
+    p = __ffma2_rn(p, t, f2(-1.13520398f));
+    p = __ffma2_rn(p, t, f2(0.27886807f));
+    p = __ffma2_rn(p, t, f2(-0.18628806f));
+    p = __ffma2_rn(p, t, f2(0.09678418f));
+    p = __ffma2_rn(p, t, f2(0.37409196f));
+    p = __ffma2_rn(p, t, f2(1.00002368f));
+    p = __ffma2_rn(p, t, f2(-1.26551223f));
+    const float2 a = __ffma2_rn(make_float2(-ax.x, -ax.y), ax, p);
+    const float2 y = __fmul2_rn(t, make_float2(__expf(a.x), __expf(a.y)));
+    return make_float2(x.x >= 0.0f ? y.x : 2.0f - y.x, x.y >= 0.0f ? y.y : 2.0f - y.y);
+}
+
+__device__ __forceinline__ float2 gelu2(float2 z)
+{
+    return __fmul2_rn(__fmul2_rn(f2(0.5f), z), erfc_nr2(__fmul2_rn(f2(-0.70710678118654752f), z)));
+}
+
+__device__ __forceinline__ float2 gelu_grad2(float2 z)
+{
+    const float2 e = make_float2(__expf(-0.5f * z.x * z.x), __expf(-0.5f * z.y * z.y));
+    return __ffma2_rn(__fmul2_rn(z, f2(0.39894228040143268f)), e,
+                      __fmul2_rn(f2(0.5f), erfc_nr2(__fmul2_rn(f2(-0.70710678118654752f), z))));
 }
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -171,167 +229,386 @@ __device__ __forceinline__ void load_halo(bf16* hs, const bf16* __restrict__ in,
 
 // ---------------------------------------------------------------------------------
 // Layer 1 (FP32 units): z_1 = conv3x3((phi, 20u, 20v), W_1) + b_1, a_1 = GELU(z_1).
+// Two pixels per thread; the weights sit transposed in shared memory (wt[k][co]) so one
+// 16-byte load feeds eight FMAs (four channels of two pixels).
+// (pixel indices fit in 32 bits: batch * ny * nx * 32 < 2^31 is checked on the host)
+__device__ __forceinline__ void gather27(const float* __restrict__ phi, const float* __restrict__ u,
+                                         const float* __restrict__ v, int p, int H, int W, float* in)
+{
+    const int r = p / W, x = p - r * W;
+    const int b = r / H, y = r - b * H;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const int row = (b * H + wrap1(y + j - 1, H)) * W;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const int q = row + wrap1(x + i - 1, W);
+            in[j * 3 + i] = phi[q];
+            in[9 + j * 3 + i] = u[q] * U_SCALE;
+            in[18 + j * 3 + i] = v[q] * U_SCALE;
+        }
+    }
+}
+
 __global__ void __launch_bounds__(256) surr_in_fwd(const float* __restrict__ phi, const float* __restrict__ u,
                                                    const float* __restrict__ v, const float* __restrict__ params,
                                                    bf16* __restrict__ z1, bf16* __restrict__ a1, int B, int H, int W)
 {
-    __shared__ float w[L1_N];
-    for (int k = threadIdx.x; k < L1_N; k += blockDim.x) w[k] = params[OFF_W1 + k];
+    __shared__ __align__(16) float wt[27][C];
+    __shared__ __align__(16) float bs[C];
+    for (int k = threadIdx.x; k < 864; k += blockDim.x) wt[k % 27][k / 27] = params[OFF_W1 + k];
+    if (threadIdx.x < C) bs[threadIdx.x] = params[OFF_W1 + 864 + threadIdx.x];
     __syncthreads();
-    const long long P = (long long)B * H * W;
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < P; p += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(p % W);
-        const long long r = p / W;
-        const int y = (int)(r % H);
-        const long long b = r / H;
-        float in[27];
+    const int P = B * H * W, pairs = (P + 1) / 2;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < pairs; t += gridDim.x * blockDim.x) {
+        const int p0 = 2 * t;
+        const bool has1 = p0 + 1 < P;
+        float in0[27], in1[27];
+        gather27(phi, u, v, p0, H, W, in0);
+        gather27(phi, u, v, has1 ? p0 + 1 : p0, H, W, in1);
+        float2 in2[27];
 #pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            const int yy = wrap1(y + j - 1, H);
-#pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                const long long q = (b * H + yy) * W + wrap1(x + i - 1, W);
-                in[j * 3 + i] = phi[q];
-                in[9 + j * 3 + i] = u[q] * U_SCALE;
-                in[18 + j * 3 + i] = v[q] * U_SCALE;
-            }
-        }
-        uint4* zo = reinterpret_cast<uint4*>(z1 + p * C);
-        uint4* ao = reinterpret_cast<uint4*>(a1 + p * C);
+        for (int k = 0; k < 27; ++k) in2[k] = make_float2(in0[k], in1[k]);
 #pragma unroll 1
-        for (int k4 = 0; k4 < 4; ++k4) { // eight output channels per 16-byte store
-            unsigned zw[4], aw[4];
+        for (int cb = 0; cb < 4; ++cb) { // eight output channels per 16-byte store
+            float2 s2[8];                // {pixel 0, pixel 1} of channel cb * 8 + c
+#pragma unroll
+            for (int c = 0; c < 8; ++c) s2[c] = f2(bs[cb * 8 + c]);
+#pragma unroll
+            for (int k = 0; k < 27; ++k) {
+                const float4 wa = *reinterpret_cast<const float4*>(&wt[k][cb * 8]);
+                const float4 wb = *reinterpret_cast<const float4*>(&wt[k][cb * 8 + 4]);
+                const float w8[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+#pragma unroll
+                for (int c = 0; c < 8; ++c) s2[c] = __ffma2_rn(f2(w8[c]), in2[k], s2[c]);
+            }
+            unsigned z0w[4], a0w[4], z1w[4], a1w[4];
 #pragma unroll
             for (int h = 0; h < 4; ++h) {
-                const int co = k4 * 8 + h * 2;
-                float s0 = w[864 + co], s1 = w[864 + co + 1];
-#pragma unroll
-                for (int k = 0; k < 27; ++k) {
-                    s0 = fmaf(w[co * 27 + k], in[k], s0);
-                    s1 = fmaf(w[(co + 1) * 27 + k], in[k], s1);
-                }
-                zw[h] = pack_bf16(s0, s1);
-                aw[h] = pack_bf16(gelu_f(s0), gelu_f(s1));
+                const float2 ga = gelu2(s2[2 * h]), gb = gelu2(s2[2 * h + 1]);
+                z0w[h] = pack_bf16(s2[2 * h].x, s2[2 * h + 1].x);
+                z1w[h] = pack_bf16(s2[2 * h].y, s2[2 * h + 1].y);
+                a0w[h] = pack_bf16(ga.x, gb.x);
+                a1w[h] = pack_bf16(ga.y, gb.y);
             }
-            if (z1) zo[k4] = make_uint4(zw[0], zw[1], zw[2], zw[3]);
-            ao[k4] = make_uint4(aw[0], aw[1], aw[2], aw[3]);
+            if (z1) reinterpret_cast<uint4*>(z1 + (size_t)p0 * C)[cb] = make_uint4(z0w[0], z0w[1], z0w[2], z0w[3]);
+            reinterpret_cast<uint4*>(a1 + (size_t)p0 * C)[cb] = make_uint4(a0w[0], a0w[1], a0w[2], a0w[3]);
+            if (has1) {
+                if (z1) reinterpret_cast<uint4*>(z1 + (size_t)(p0 + 1) * C)[cb] = make_uint4(z1w[0], z1w[1], z1w[2], z1w[3]);
+                reinterpret_cast<uint4*>(a1 + (size_t)(p0 + 1) * C)[cb] = make_uint4(a1w[0], a1w[1], a1w[2], a1w[3]);
+            }
         }
     }
 }
 
 // ---------------------------------------------------------------------------------
-// Layers 2-4 on the tensor cores. out[p][n] = sum_tap sum_k wpk[tap][n][k] in[p + off(tap)][k]
-// with off(tap) = (tap / 3 - 1, tap % 3 - 1).
-//   MODE_FWD:   z = out + bias; stores z (if out_z) and GELU(z) (out_a), BF16.
-//   MODE_DGRAD: out is dL/da of the layer below; stores dL/dz = out * GELU'(zaux), BF16.
-// Each warp owns two tile rows (two m16 tiles of 16 pixels) and all 32 output channels.
-enum { MODE_FWD = 0, MODE_DGRAD = 1 };
+// tcgen05 (fifth-generation tensor core) helpers. Operands sit in shared memory in the
+// no-swizzle K-major layout: "core matrices" of 8 rows x 16 bytes (8 BF16 along K),
+// 16 bytes per row; the descriptor gives the byte distance between core matrices
+// adjacent along K (leading) and along M or N (stride). Accumulators live in tensor
+// memory (TMEM): lane = row of D, column = column of D.
 
-template <int MODE>
-__global__ void __launch_bounds__(CONV_THREADS, 3) surr_conv_mma(const bf16* __restrict__ in, const bf16* __restrict__ wpk,
-                                                              const float* __restrict__ bias,
-                                                              const bf16* __restrict__ zaux, bf16* __restrict__ out_z,
-                                                              bf16* __restrict__ out_a, const Geo g)
+__device__ __forceinline__ uint64_t umma_desc(unsigned saddr, unsigned lbo, unsigned sbo)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
-    bf16* ws = reinterpret_cast<bf16*>(smem);
-    bf16* hs = ws + W_SMEM;
+    return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of kind::f16: FP32 D, BF16 A and B, both K-major, M x N.
+__host__ __device__ constexpr unsigned umma_idesc(int m, int n)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(n >> 3) << 17) | ((unsigned)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(unsigned tmem, uint64_t ad, uint64_t bd, unsigned idesc, unsigned acc)
+{
+    asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                 "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n"
+                 ::"r"(tmem), "l"(ad), "l"(bd), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void umma_commit(unsigned mbar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mbar) : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+
+// Wait for the phase `parity` of an mbarrier, giving up after ~1 s of SM clock. Each
+// try_wait may suspend the warp for up to 0.1 ms (a hint to the hardware), so a waiting
+// warp does not spin on the issue slots.
+__device__ __forceinline__ bool mbar_wait(unsigned mbar, unsigned parity)
+{
+    const long long t0 = clock64();
+    for (;;) {
+        unsigned done;
+        asm volatile("{\n.reg .pred q;\nmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2, %3;\nselp.u32 %0, 1, 0, q;\n}\n"
+                     : "=r"(done) : "r"(mbar), "r"(parity), "r"(100000u) : "memory");
+        if (done) return true;
+        if (clock64() - t0 > 2000000000LL) return false;
+    }
+}
+
+#define TMEM_LD_OUT16(r) "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), \
+    "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+
+// 32 consecutive TMEM columns (x32) or 16 (x16) of this thread's lane.
+__device__ __forceinline__ void tmem_ld32(unsigned ta, unsigned* r)
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                 "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+                 : TMEM_LD_OUT16(r), TMEM_LD_OUT16((r + 16)) : "r"(ta));
+}
+__device__ __forceinline__ void tmem_ld16(unsigned ta, unsigned* r)
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+                 : TMEM_LD_OUT16(r) : "r"(ta));
+}
+__device__ __forceinline__ void tmem_ld8(unsigned ta, unsigned* r)
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(ta));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory"); }
+
+// ---------------------------------------------------------------------------------
+// Layers 2-5 on the tensor cores: implicit GEMM, one MMA of M = 128 pixels (one row
+// segment of a tile), N output channels, K = 16 input channels per tap and K-half:
+//   out[p][n] = sum_tap sum_k w[tap][n][k] in[p + off(tap)][k],  off(tap) = (tap/3 - 1, tap%3 - 1).
+// A tile is UR = 4 rows x 128 columns of one image. Its (UR+2) x 130 x 32 halo is staged
+// by cp.async as four planes of 16-byte channel chunks, so the window of any tap is a
+// set of core matrices 16 bytes apart along M (SBO 128 bytes per 8 pixels) and one
+// plane apart along K. Weights: [tap][chunk][n][8] (block per tap and chunk).
+//
+// One persistent CTA per SM (the occupancy of tcgen05 kernels), warp-specialised:
+//   warps 0-3   load halos into a two-stage ring (cp.async; each thread waits for its
+//               own copies, fences them into the async proxy and arrives on full[s]);
+//   warp 4      one thread issues the 4 x 9 x 2 MMAs of a tile into one of two TMEM
+//               accumulator sets and commits them to empty[s] (stage free) and
+//               tfull[a] (accumulators ready);
+//   warps 5-20  read the accumulators (warp w: TMEM lanes 32 (w % 4).., tile row
+//               (w - 5) / 4; one pixel per thread, eight channels per tcgen05.ld), apply
+//               the epilogue, write 16 bytes per pixel and group and arrive on tempty[a].
+// Every mbarrier wait gives up after ~1 s; the CTA then records the failure, drains
+// and frees its tensor memory.
+//   MODE_FWD (N = 32):  z = acc + b; stores z (if out_z) and GELU(z), BF16.
+//   MODE_DGRAD (N = 32): acc is dL/da of the layer below; stores acc GELU'(zaux), BF16.
+//   MODE_OUT (N = 16, only n = 0 real): z_5 = acc + b_5 (FP32) and 16 partial sums per
+//               tile (one per epilogue warp) in tsum[16 tile + e].
+enum { MODE_FWD = 0, MODE_DGRAD = 1, MODE_OUT = 2 };
+constexpr int UR = 4, UW = 128, UHR = UR + 2, UHW = UW + 2;
+constexpr int UPX = UHR * UHW;            // halo pixels (780)
+constexpr int UPLANE = UPX * 16;          // bytes of one channel-chunk plane
+constexpr int UHALO = 4 * UPLANE;         // bytes of one halo stage
+constexpr int U_LOAD_WARPS = 4, U_EPI_WARPS = 16;
+constexpr int UMMA_THREADS = (U_LOAD_WARPS + 1 + U_EPI_WARPS) * 32;
+constexpr int U_TSUM = U_EPI_WARPS;       // partial sums per tile (MODE_OUT)
+
+struct UGeo {
+    int B, H, W;
+    int tx, ty;           // tiles per image along x and y
+    long long ntiles;
+};
+
+inline UGeo make_ugeo(int B, int H, int W)
+{
+    UGeo g;
+    g.B = B; g.H = H; g.W = W;
+    g.tx = (W + UW - 1) / UW;
+    g.ty = (H + UR - 1) / UR;
+    g.ntiles = (long long)B * g.tx * g.ty;
+    return g;
+}
+
+template <int N>
+constexpr int umma_smem_bytes() { return 9 * 4 * N * 16 + 2 * UHALO; }
+
+__device__ __forceinline__ void mbar_init(unsigned mbar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(mbar), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive(unsigned mbar)
+{
+    asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(mbar) : "memory");
+}
+
+template <int MODE, int N>
+__global__ void __launch_bounds__(UMMA_THREADS, 1) surr_conv_umma(const bf16* __restrict__ in, const bf16* __restrict__ wu,
+                                                                  const float* __restrict__ bias,
+                                                                  const bf16* __restrict__ zaux, bf16* __restrict__ out_z,
+                                                                  bf16* __restrict__ out_a, float* __restrict__ z5,
+                                                                  double* __restrict__ tsum, const UGeo g,
+                                                                  int* __restrict__ err)
+{
+    constexpr int WBYTES = 9 * 4 * N * 16;
+    constexpr int NSET = UR * N;          // TMEM columns of one accumulator set
+    constexpr int NCOL = 2 * NSET;        // two sets (a power of two >= 32)
+    constexpr unsigned IDESC = umma_idesc(UW, N);
+    extern __shared__ __align__(128) unsigned char smem[];
+    unsigned char* ws = smem;
+    unsigned char* hs = smem + WBYTES;    // stage s at hs + s * UHALO
+    __shared__ __align__(8) unsigned long long bars[8]; // full[2], empty[2], tfull[2], tempty[2]
+    __shared__ unsigned tslot;
+    __shared__ float bv[32];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int gid = lane >> 2, tid4 = lane & 3;
-    const int lq = lane >> 3, lr = lane & 7;
+    const unsigned b_full = smem_u32(&bars[0]), b_empty = smem_u32(&bars[2]);
+    const unsigned b_tfull = smem_u32(&bars[4]), b_tempty = smem_u32(&bars[6]);
 
-    for (int k = tid; k < 9 * C * 4; k += CONV_THREADS) {
-        const int row = k >> 2, part = k & 3;
-        cp_async16(ws + row * PS + part * 8, wpk + row * C + part * 8);
-    }
-    long long tile = blockIdx.x;
-    int buf = 0;
-    if (tile < g.ntiles) load_halo(hs, in, g, tile, tid, CONV_THREADS);
+    for (int k = tid; k < WBYTES / 16; k += UMMA_THREADS) cp_async16(ws + k * 16, wu + k * 8);
     cp_commit();
-
-    float bv[8];
-    if (MODE == MODE_FWD) {
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt) {
-            bv[2 * nt] = bias[nt * 8 + 2 * tid4];
-            bv[2 * nt + 1] = bias[nt * 8 + 2 * tid4 + 1];
+    if (tid < 32) bv[tid] = (MODE == MODE_FWD || (MODE == MODE_OUT && tid == 0)) ? bias[tid] : 0.0f;
+    if (tid == 0) {
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(b_full + 8 * s, U_LOAD_WARPS * 32);
+            mbar_init(b_empty + 8 * s, 1);
+            mbar_init(b_tfull + 8 * s, 1);
+            mbar_init(b_tempty + 8 * s, U_EPI_WARPS);
         }
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
-
-    const unsigned ws_base = smem_u32(ws);
-    for (; tile < g.ntiles; tile += gridDim.x) {
-        const long long next = tile + gridDim.x;
-        if (next < g.ntiles) load_halo(hs + (buf ^ 1) * (HPX * PS), in, g, next, tid, CONV_THREADS);
-        cp_commit();
-        cp_wait<1>();
-        __syncthreads();
-
-        const unsigned hs_base = smem_u32(hs + buf * (HPX * PS));
-        float acc[2][4][4];
-#pragma unroll
-        for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-            for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-                for (int e = 0; e < 4; ++e) acc[mt][nt][e] = 0.0f;
-
-        const int r0 = warp * 2;
-        // per-lane ldmatrix row addresses at tap (0, 0), k-half 0; every (tap, k-half)
-        // adds a compile-time byte offset
-        const unsigned a_addr = hs_base + (unsigned)(((r0 * HWD + (lq & 1) * 8 + lr) * PS + (lq >> 1) * 8) * 2);
-        const unsigned b_addr = ws_base + (unsigned)((((lq >> 1) * 8 + lr) * PS + (lq & 1) * 8) * 2);
-#pragma unroll
-        for (int tap = 0; tap < 9; ++tap) {
-            const int j = tap / 3, i = tap % 3;
-#pragma unroll
-            for (int kh = 0; kh < 2; ++kh) {
-                unsigned a[2][4];
-#pragma unroll
-                for (int mt = 0; mt < 2; ++mt)
-                    ldsm_x4(a_addr + (unsigned)((((mt + j) * HWD + i) * PS + kh * 16) * 2), a[mt][0], a[mt][1], a[mt][2],
-                            a[mt][3]);
-                unsigned bfr[4][2];
-#pragma unroll
-                for (int nb = 0; nb < 2; ++nb)
-                    ldsm_x4(b_addr + (unsigned)(((tap * C + nb * 16) * PS + kh * 16) * 2), bfr[2 * nb][0],
-                            bfr[2 * nb][1], bfr[2 * nb + 1][0], bfr[2 * nb + 1][1]);
-#pragma unroll
-                for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-                    for (int nt = 0; nt < 4; ++nt) mma_bf16(acc[mt][nt], a[mt], bfr[nt][0], bfr[nt][1]);
-            }
-        }
-
-        int b, y0, x0;
-        tile_origin(g, tile, b, y0, x0);
-#pragma unroll
-        for (int mt = 0; mt < 2; ++mt) {
-            const int y = y0 + r0 + mt;
-#pragma unroll
-            for (int hf = 0; hf < 2; ++hf) {
-                const int x = x0 + gid + hf * 8;
-                if (y >= g.H || x >= g.W) continue;
-                const size_t base = (((size_t)b * g.H + y) * g.W + x) * C;
-#pragma unroll
-                for (int nt = 0; nt < 4; ++nt) {
-                    const int co = nt * 8 + 2 * tid4;
-                    const float c0 = acc[mt][nt][2 * hf], c1 = acc[mt][nt][2 * hf + 1];
-                    if (MODE == MODE_FWD) {
-                        const float z0 = c0 + bv[2 * nt], z1 = c1 + bv[2 * nt + 1];
-                        if (out_z) *reinterpret_cast<unsigned*>(out_z + base + co) = pack_bf16(z0, z1);
-                        *reinterpret_cast<unsigned*>(out_a + base + co) = pack_bf16(gelu_f(z0), gelu_f(z1));
-                    } else {
-                        const float2 z = unpack_bf16(*reinterpret_cast<const unsigned*>(zaux + base + co));
-                        *reinterpret_cast<unsigned*>(out_a + base + co) =
-                            pack_bf16(c0 * gelu_grad_f(z.x), c1 * gelu_grad_f(z.y));
-                    }
-                }
-            }
-        }
-        __syncthreads();
-        buf ^= 1;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tslot)), "n"(NCOL));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::);
     }
     cp_wait<0>();
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); // weights -> tensor core reads
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const unsigned tmem = tslot;
+    const int per = g.tx * g.ty;
+    bool failed = false;
+
+    if (warp < U_LOAD_WARPS) {
+        // ---- loaders: thread lt copies channel chunk kc = lt % 4 of halo columns
+        // hc = lt / 4 + 32 m (m < 5, hc < 130) in all six halo rows
+        const int kc = tid & 3, hc0 = tid >> 2;
+        long long k = 0;
+        for (long long tile = blockIdx.x; tile < g.ntiles; tile += gridDim.x, ++k) {
+            const int s = (int)(k & 1);
+            if (k >= 2 && !mbar_wait(b_empty + 8 * s, (unsigned)(((k >> 1) - 1) & 1))) { failed = true; break; }
+            const int b = (int)tile / per;
+            const int rem = (int)tile - b * per;
+            const int y0 = (rem / g.tx) * UR, x0 = (rem - (rem / g.tx) * g.tx) * UW;
+            unsigned char* st = hs + s * UHALO + kc * UPLANE;
+            int xo[5];
+#pragma unroll
+            for (int m = 0; m < 5; ++m) xo[m] = wrap_halo(x0 + hc0 + 32 * m - 1, g.W);
+#pragma unroll
+            for (int hr = 0; hr < UHR; ++hr) {
+                const bf16* row = in + (((size_t)b * g.H + wrap_halo(y0 + hr - 1, g.H)) * g.W) * C + kc * 8;
+#pragma unroll
+                for (int m = 0; m < 5; ++m) {
+                    const int hc = hc0 + 32 * m;
+                    if (hc < UHW) cp_async16(st + (hr * UHW + hc) * 16, row + (size_t)xo[m] * C);
+                }
+            }
+            cp_commit();
+            cp_wait<0>();
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            mbar_arrive(b_full + 8 * s);
+        }
+    } else if (warp == U_LOAD_WARPS) {
+        // ---- MMA issuer
+        if (lane == 0) {
+            const unsigned ws_s = smem_u32(ws), hs_s = smem_u32(hs);
+            long long k = 0;
+            for (long long tile = blockIdx.x; tile < g.ntiles; tile += gridDim.x, ++k) {
+                const int s = (int)(k & 1);
+                if (!mbar_wait(b_full + 8 * s, (unsigned)((k >> 1) & 1))) { failed = true; break; }
+                if (k >= 2 && !mbar_wait(b_tempty + 8 * s, (unsigned)(((k >> 1) - 1) & 1))) { failed = true; break; }
+                tc_fence_after();
+                const uint64_t a0 = umma_desc(hs_s + (unsigned)(s * UHALO), UPLANE, 128), b0 = umma_desc(ws_s, N * 16, 128);
+                const unsigned acc = tmem + (unsigned)(s * NSET);
+#pragma unroll
+                for (int r = 0; r < UR; ++r)
+#pragma unroll
+                    for (int tap = 0; tap < 9; ++tap)
+#pragma unroll
+                        for (int kh = 0; kh < 2; ++kh) {
+                            const unsigned aoff = (unsigned)(2 * kh * UPLANE + ((r + tap / 3) * UHW + tap % 3) * 16) >> 4;
+                            const unsigned boff = (unsigned)((tap * 4 + 2 * kh) * N * 16) >> 4;
+                            umma_bf16(acc + (unsigned)(r * N), a0 + aoff, b0 + boff, IDESC, (tap | kh) != 0);
+                        }
+                umma_commit(b_empty + 8 * s);
+                umma_commit(b_tfull + 8 * s);
+            }
+        }
+        __syncwarp();
+    } else {
+        // ---- epilogue
+        const int e = warp - U_LOAD_WARPS - 1;          // 0 .. 15
+        const int q4 = warp & 3, r = e >> 2;
+        long long k = 0;
+        for (long long tile = blockIdx.x; tile < g.ntiles; tile += gridDim.x, ++k) {
+            const int s = (int)(k & 1);
+            if (!mbar_wait(b_tfull + 8 * s, (unsigned)((k >> 1) & 1))) { failed = true; break; }
+            tc_fence_after();
+            const int b = (int)tile / per;
+            const int rem = (int)tile - b * per;
+            const int y = (rem / g.tx) * UR + r, x = (rem - (rem / g.tx) * g.tx) * UW + 32 * q4 + lane;
+            const bool valid = y < g.H && x < g.W;
+            const size_t p = valid ? ((size_t)b * g.H + y) * g.W + x : 0;
+            const unsigned ta = tmem + ((unsigned)(32 * q4) << 16) + (unsigned)(s * NSET + r * N);
+            double psum = 0.0;
+            if (MODE == MODE_OUT) {
+                unsigned v[8];
+                tmem_ld8(ta, v);
+                tmem_wait_ld();
+                if (valid) {
+                    const float z = __uint_as_float(v[0]) + bv[0];
+                    z5[p] = z;
+                    psum = z;
+                }
+            } else {
+#pragma unroll 1
+                for (int k4 = 0; k4 < 4; ++k4) {
+                    unsigned v[8];
+                    tmem_ld8(ta + (unsigned)(k4 * 8), v);
+                    tmem_wait_ld();
+                    unsigned o[4], zw[4];
+                    if (!valid) {
+                    } else if (MODE == MODE_FWD) {
+#pragma unroll
+                        for (int h = 0; h < 4; ++h) {
+                            const int c = k4 * 8 + h * 2;
+                            const float2 z = __fadd2_rn(make_float2(__uint_as_float(v[2 * h]), __uint_as_float(v[2 * h + 1])),
+                                                        make_float2(bv[c], bv[c + 1]));
+                            zw[h] = pack_bf16(z.x, z.y);
+                            const float2 a = gelu2(z);
+                            o[h] = pack_bf16(a.x, a.y);
+                        }
+                        if (out_z) reinterpret_cast<uint4*>(out_z + p * C)[k4] = make_uint4(zw[0], zw[1], zw[2], zw[3]);
+                    } else {
+                        const uint4 zv = reinterpret_cast<const uint4*>(zaux + p * C)[k4];
+                        const unsigned zz[4] = {zv.x, zv.y, zv.z, zv.w};
+#pragma unroll
+                        for (int h = 0; h < 4; ++h) {
+                            const float2 d = __fmul2_rn(make_float2(__uint_as_float(v[2 * h]), __uint_as_float(v[2 * h + 1])),
+                                                        gelu_grad2(unpack_bf16(zz[h])));
+                            o[h] = pack_bf16(d.x, d.y);
+                        }
+                    }
+                    if (valid) reinterpret_cast<uint4*>(out_a + p * C)[k4] = make_uint4(o[0], o[1], o[2], o[3]);
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(b_tempty + 8 * s);
+            if (MODE == MODE_OUT) {
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) psum += __shfl_down_sync(0xffffffffu, psum, o);
+                if (lane == 0) tsum[(size_t)tile * U_TSUM + e] = psum;
+            }
+        }
+    }
+    if (failed) atomicExch(err, 1);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "n"(NCOL));
 }
 
 // ---------------------------------------------------------------------------------
@@ -344,7 +621,7 @@ __global__ void __launch_bounds__(CONV_THREADS, 3) surr_conv_mma(const bf16* __r
 __global__ void __launch_bounds__(WG_THREADS) surr_wgrad_mma(const bf16* __restrict__ gz, const bf16* __restrict__ a,
                                                              float* __restrict__ part, const Geo g)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     bf16* gs = reinterpret_cast<bf16*>(smem);     // [256][PS]
     bf16* hs = gs + TH * TW * PS;                  // [324][PS]
     __shared__ float bsum[8][C];
@@ -446,59 +723,30 @@ __device__ __forceinline__ double block_sum(double v, double* red)
     return s; // valid in thread 0
 }
 
-__global__ void __launch_bounds__(256) surr_out_fwd(const bf16* __restrict__ a4, const float* __restrict__ params,
-                                                    float* __restrict__ z5, double* __restrict__ part, int H, int W)
+// Deterministic sum of n doubles by one warp (fixed assignment and butterfly order).
+__device__ __forceinline__ double warp_sum_ordered(const double* v, int n)
 {
-    __shared__ float w[L5_N];
-    __shared__ double red[8];
-    for (int k = threadIdx.x; k < L5_N; k += blockDim.x) w[k] = params[OFF_W5 + k];
-    __syncthreads();
-    const int b = blockIdx.y;
-    const long long HWn = (long long)H * W;
+    const int lane = threadIdx.x & 31;
     double s = 0.0;
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < HWn; q += (long long)gridDim.x * blockDim.x) {
-        const int y = (int)(q / W), x = (int)(q % W);
-        float acc = w[288];
-#pragma unroll 1
-        for (int tap = 0; tap < 9; ++tap) {
-            const int yy = wrap1(y + tap / 3 - 1, H), xx = wrap1(x + tap % 3 - 1, W);
-            const uint4* src = reinterpret_cast<const uint4*>(a4 + (((size_t)b * H + yy) * W + xx) * C);
+    for (int k = lane; k < n; k += 32) s += v[k];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const uint4 v = src[k];
-                const unsigned vv[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-                for (int h = 0; h < 4; ++h) {
-                    const float2 f = unpack_bf16(vv[h]);
-                    const int ci = k * 8 + h * 2;
-                    acc = fmaf(w[ci * 9 + tap], f.x, acc);
-                    acc = fmaf(w[(ci + 1) * 9 + tap], f.y, acc);
-                }
-            }
-        }
-        z5[(size_t)b * HWn + q] = acc;
-        s += acc;
-    }
-    s = block_sum(s, red);
-    if (threadIdx.x == 0) part[(size_t)b * gridDim.x + blockIdx.x] = s;
-}
-
-__device__ __forceinline__ double image_sum(const double* part, int nb)
-{
-    double s = 0.0;
-    for (int k = 0; k < nb; ++k) s += part[k];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     return s;
 }
 
-// phi_out = phi + (z_5 - mean(z_5)) per image.
+// phi_out = phi + (z_5 - mean(z_5)) per image; tsum holds partial sums of z_5, those of
+// image b being [b * tpi, (b + 1) * tpi).
 __global__ void __launch_bounds__(256) surr_residual(const float* __restrict__ phi, const float* __restrict__ z5,
-                                                     const double* __restrict__ part, float* __restrict__ out, int H,
-                                                     int W)
+                                                     const double* __restrict__ tsum, int tpi,
+                                                     float* __restrict__ out, int H, int W)
 {
     __shared__ double mean;
     const int b = blockIdx.y;
     const long long HWn = (long long)H * W;
-    if (threadIdx.x == 0) mean = image_sum(part + (size_t)b * gridDim.x, gridDim.x) / (double)HWn;
+    if (threadIdx.x < 32) {
+        const double s = warp_sum_ordered(tsum + (size_t)b * tpi, tpi);
+        if (threadIdx.x == 0) mean = s / (double)HWn;
+    }
     __syncthreads();
     const double m = mean;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < HWn; q += (long long)gridDim.x * blockDim.x) {
@@ -538,7 +786,10 @@ __global__ void __launch_bounds__(256) surr_gz5(const float* __restrict__ out, c
     __shared__ double mean;
     const int b = blockIdx.y;
     const long long HWn = (long long)H * W;
-    if (threadIdx.x == 0) mean = image_sum(gpart + (size_t)b * gridDim.x, gridDim.x) / (double)HWn;
+    if (threadIdx.x < 32) {
+        const double sm = warp_sum_ordered(gpart + (size_t)b * gridDim.x, gridDim.x);
+        if (threadIdx.x == 0) mean = sm / (double)HWn;
+    }
     __syncthreads();
     const float m = (float)mean;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < HWn; q += (long long)gridDim.x * blockDim.x) {
@@ -554,12 +805,13 @@ __global__ void __launch_bounds__(256) surr_out_bwd(const bf16* __restrict__ a4,
                                                     const float* __restrict__ gz5, const float* __restrict__ params,
                                                     bf16* __restrict__ gz4, float* __restrict__ part, const Geo g)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(128) unsigned char smem[];
     bf16* hs = reinterpret_cast<bf16*>(smem);          // a_4 halo [324][PS]
     __shared__ float gh[HPX];                           // gz5 halo
     __shared__ float w[L5_N];
     const int tid = threadIdx.x;
-    for (int k = tid; k < L5_N; k += blockDim.x) w[k] = params[OFF_W5 + k];
+    for (int k = tid; k < L5_N; k += blockDim.x)
+        w[k] = k < 288 ? __bfloat162float(__float2bfloat16_rn(params[OFF_W5 + k])) : params[OFF_W5 + k];
     float acc0 = 0.0f, acc1 = 0.0f;
     const int k0 = tid, k1 = tid + 256; // outputs of this thread (k1 valid when < 289)
     for (long long tile = blockIdx.x; tile < g.ntiles; tile += gridDim.x) {
@@ -698,13 +950,25 @@ __global__ void __launch_bounds__(256) surr_in_wgrad(const bf16* __restrict__ gz
     }
 }
 
-// grad[k] = sum over CTAs of part[cta][k] (FP64, fixed order).
-__global__ void surr_reduce(const float* __restrict__ part, int ncta, int stride, int count, float* __restrict__ grad)
+// grad[k] = sum over c < ncta of part[c][k] in FP64. A block owns 32 consecutive k;
+// thread (kx, cy) sums c = cy, cy + 8, ... in order, and the eight sums are added in
+// order of cy (deterministic).
+__global__ void __launch_bounds__(256) surr_reduce(const float* __restrict__ part, int ncta, int stride, int count,
+                                                   float* __restrict__ grad)
 {
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < count; k += gridDim.x * blockDim.x) {
-        double s = 0.0;
-        for (int c = 0; c < ncta; ++c) s += (double)part[(size_t)c * stride + k];
-        grad[k] = (float)s;
+    __shared__ double sm[8][33];
+    const int kx = threadIdx.x & 31, cy = threadIdx.x >> 5;
+    const int k = blockIdx.x * 32 + kx;
+    double acc = 0.0;
+    if (k < count)
+        for (int c = cy; c < ncta; c += 8) acc += (double)part[(size_t)c * stride + k];
+    sm[cy][kx] = acc;
+    __syncthreads();
+    if (cy == 0 && k < count) {
+        double t = 0.0;
+#pragma unroll
+        for (int y = 0; y < 8; ++y) t += sm[y][kx];
+        grad[k] = (float)t;
     }
 }
 
@@ -722,17 +986,26 @@ __global__ void surr_adam(float* __restrict__ p, float* __restrict__ m, float* _
     }
 }
 
-// BF16 copies of W_2..W_4 for the tensor-core kernels: forward layout wf[l][tap][co][ci]
-// and input-gradient layout wd[l][tap'][ci][co] = W[co][ci][8 - tap'].
-__global__ void surr_pack(const float* __restrict__ p, bf16* __restrict__ wf, bf16* __restrict__ wd)
+// BF16 tensor-core operands in the [tap][chunk][n][8] layout of surr_conv_umma:
+//   wu[l]  (forward, n = co, K = ci):       W_l[co][8 chunk + e][tap]
+//   wdu[l] (input gradient, n = ci, K = co): W_l[8 chunk + e][ci][8 - tap]
+//   w5u    (layer 5, n < 16, only n = 0):   W_5[0][8 chunk + e][tap]
+__global__ void surr_pack(const float* __restrict__ p, bf16* __restrict__ wu, bf16* __restrict__ wdu,
+                          bf16* __restrict__ w5u)
 {
-    const int n = 3 * 9 * C * C;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-        const int l = k / (9 * C * C), r = k % (9 * C * C);
-        const int co = r / (C * 9), ci = (r / 9) % C, tap = r % 9;
-        const bf16 w = __float2bfloat16_rn(p[OFF_W2 + l * LH_N + r]);
-        wf[(size_t)l * 9 * C * C + (tap * C + co) * C + ci] = w;
-        wd[(size_t)l * 9 * C * C + ((8 - tap) * C + ci) * C + co] = w;
+    const int n_hidden = 3 * 9 * C * C, n5 = 9 * 4 * 16 * 8;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n_hidden + n5; k += gridDim.x * blockDim.x) {
+        if (k < n_hidden) {
+            const int l = k / (9 * C * C), r = k % (9 * C * C);
+            const int tap = r / (4 * C * 8), kc = (r / (C * 8)) % 4, n = (r / 8) % C, e = r % 8;
+            const float* W = p + OFF_W2 + l * LH_N;                  // [co][ci][tap]
+            wu[k] = __float2bfloat16_rn(W[(n * C + kc * 8 + e) * 9 + tap]);
+            wdu[k] = __float2bfloat16_rn(W[((kc * 8 + e) * C + n) * 9 + (8 - tap)]);
+        } else {
+            const int r = k - n_hidden;
+            const int tap = r / (4 * 16 * 8), kc = (r / (16 * 8)) % 4, n = (r / 8) % 16, e = r % 8;
+            w5u[r] = __float2bfloat16_rn(n == 0 ? p[OFF_W5 + (kc * 8 + e) * 9 + tap] : 0.0f);
+        }
     }
 }
 
@@ -742,15 +1015,15 @@ __global__ void __launch_bounds__(256) surr_metrics(const float* __restrict__ ph
                                                     double* __restrict__ part)
 {
     __shared__ double red[8];
-    const long long HWn = (long long)H * W;
+    const int HWn = H * W;
     double sm = 0.0, sp = 0.0, sgr = 0.0;
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < HWn; q += (long long)gridDim.x * blockDim.x) {
-        const int y = (int)(q / W), x = (int)(q % W);
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < HWn; q += gridDim.x * blockDim.x) {
+        const int y = q / W, x = q - y * W;
         const double f = phi[q];
         sm += f;
         if (f > 0.05 && f < 0.95) {
-            const double gx = 0.5 * ((double)phi[(long long)y * W + wrap1(x + 1, W)] - (double)phi[(long long)y * W + wrap1(x - 1, W)]);
-            const double gy = 0.5 * ((double)phi[(long long)wrap1(y + 1, H) * W + x] - (double)phi[(long long)wrap1(y - 1, H) * W + x]);
+            const double gx = 0.5 * ((double)phi[y * W + wrap1(x + 1, W)] - (double)phi[y * W + wrap1(x - 1, W)]);
+            const double gy = 0.5 * ((double)phi[wrap1(y + 1, H) * W + x] - (double)phi[wrap1(y - 1, H) * W + x]);
             sp += f * (1.0 - f);
             sgr += sqrt(gx * gx + gy * gy);
         }
@@ -772,6 +1045,8 @@ using namespace surr;
 // ---------------------------------------------------------------------------------
 // Host side.
 
+constexpr int HYB_DEPTH = 8; // surrogate windows run ahead of one host check
+
 struct lbm_ace_net {
     int dev = 0;
     int sms = 0;
@@ -780,8 +1055,10 @@ struct lbm_ace_net {
     float* adam_m = nullptr;
     float* adam_v = nullptr;
     float* grad = nullptr;
-    bf16* wf = nullptr;       // [3][9][32][32]
-    bf16* wd = nullptr;
+    bf16* wu = nullptr;       // tensor-core operands: [3][9][4][32][8] forward,
+    bf16* wdu = nullptr;      //   [3][9][4][32][8] input gradient,
+    bf16* w5u = nullptr;      //   [9][4][16][8] layer 5
+    int* derr = nullptr;      // set by a kernel whose bounded wait gave up
     long long adam_t = 0;
     bool have_grad = false;
     // activations, sized for cap pixels
@@ -794,12 +1071,17 @@ struct lbm_ace_net {
     float* outb = nullptr;    // phi_out of loss_grad
     double* rpart = nullptr;  int rpart_n = 0;   // per-image reduction partials
     double* rpart2 = nullptr;
+    double* tsum = nullptr;   long long tsum_n = 0; // per-tile sums of z_5
     float* wpart = nullptr;   size_t wpart_n = 0; // per-CTA gradient partials
-    int conv_grid = 0, wg_grid = 0, ob_grid = 0, iw_grid = 0;
-    size_t conv_smem = 0, wg_smem = 0, ob_smem = 0;
+    int conv_grid = 0, out_grid = 0, wg_grid = 0, ob_grid = 0, iw_grid = 0;
+    int conv_occ = 0, out_occ = 0;  // resident CTAs per SM reported for the tensor-core kernels
+    size_t conv_smem = 0, out_smem = 0, wg_smem = 0, ob_smem = 0;
     std::vector<double> hpart;
-    float* hyb[4] = {nullptr, nullptr, nullptr, nullptr}; // hybrid advance: phi, candidate, u, v
+    // hybrid advance: HYB_DEPTH + 1 phase fields (a ring), u, v, and the metric partials of
+    // HYB_DEPTH speculative windows
+    float* hyb[HYB_DEPTH + 3] = {};
     long long hyb_n = 0;
+    double* hyb_part = nullptr;
     std::string err;
 };
 
@@ -855,8 +1137,16 @@ void free_acts(lbm_ace_net* n)
     n->cap = 0;
 }
 
-int ensure_acts(lbm_ace_net* n, long long P, int B)
+int ensure_acts(lbm_ace_net* n, long long P, int B, int H = 3, int W = 3)
 {
+    const long long nt = make_ugeo(B, H, W).ntiles * U_TSUM;
+    if (nt > n->tsum_n) {
+        cudaFree(n->tsum);
+        n->tsum = nullptr;
+        n->tsum_n = 0;
+        NCK(n, cudaMalloc(&n->tsum, (size_t)nt * sizeof(double)));
+        n->tsum_n = nt;
+    }
     if (P > n->cap) {
         free_acts(n);
         const size_t act = (size_t)P * C * sizeof(bf16);
@@ -894,26 +1184,39 @@ int check_dims(lbm_ace_net* n, int B, int H, int W)
 int run_forward(lbm_ace_net* n, const float* phi, const float* u, const float* v, float* out, int B, int H, int W,
                 bool keep_z)
 {
-    const Geo g = make_geo(B, H, W);
+    const UGeo g = make_ugeo(B, H, W);
     const long long P = (long long)B * H * W;
-    surr_in_fwd<<<grid1(P, n->sms), 256, 0, n->stream>>>(phi, u, v, n->params, keep_z ? n->z[0] : nullptr, n->a[0],
+    surr_in_fwd<<<grid1((P + 1) / 2, n->sms), 256, 0, n->stream>>>(phi, u, v, n->params, keep_z ? n->z[0] : nullptr, n->a[0],
                                                          B, H, W);
     const int grid = (int)std::min<long long>(g.ntiles, n->conv_grid);
     for (int l = 0; l < 3; ++l) {
-        surr_conv_mma<MODE_FWD><<<grid, CONV_THREADS, n->conv_smem, n->stream>>>(
-            n->a[l], n->wf + (size_t)l * 9 * C * C, n->params + OFF_W2 + l * LH_N + 9216, nullptr,
-            keep_z ? n->z[l + 1] : nullptr, n->a[l + 1], g);
+        surr_conv_umma<MODE_FWD, 32><<<grid, UMMA_THREADS, n->conv_smem, n->stream>>>(
+            n->a[l], n->wu + (size_t)l * 9 * C * C, n->params + OFF_W2 + l * LH_N + 9216, nullptr,
+            keep_z ? n->z[l + 1] : nullptr, n->a[l + 1], nullptr, nullptr, g, n->derr);
     }
-    const int rb = red_blocks(H, W);
-    surr_out_fwd<<<dim3(rb, B), 256, 0, n->stream>>>(n->a[3], n->params, n->z5, n->rpart, H, W);
-    surr_residual<<<dim3(rb, B), 256, 0, n->stream>>>(phi, n->z5, n->rpart, out, H, W);
+    const int gout = (int)std::min<long long>(g.ntiles, n->out_grid);
+    surr_conv_umma<MODE_OUT, 16><<<gout, UMMA_THREADS, n->out_smem, n->stream>>>(
+        n->a[3], n->w5u, n->params + OFF_W5 + 288, nullptr, nullptr, nullptr, n->z5, n->tsum, g, n->derr);
+    surr_residual<<<dim3(red_blocks(H, W), B), 256, 0, n->stream>>>(phi, n->z5, n->tsum, (int)(g.tx * g.ty * U_TSUM),
+                                                                     out, H, W);
     NCK(n, cudaGetLastError());
+    return LBM_ACE_OK;
+}
+
+int check_err(lbm_ace_net* n)
+{
+    int e = 0;
+    NCK(n, cudaMemcpy(&e, n->derr, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e) {
+        NCK(n, cudaMemset(n->derr, 0, sizeof(int)));
+        return nfail(n, LBM_ACE_ETIMEOUT, "a tensor-core wait gave up (tcgen05 commit not observed within ~1 s)");
+    }
     return LBM_ACE_OK;
 }
 
 int repack(lbm_ace_net* n)
 {
-    surr_pack<<<grid1(3 * 9 * C * C, n->sms), 256, 0, n->stream>>>(n->params, n->wf, n->wd);
+    surr_pack<<<grid1(3 * 9 * C * C + 9 * 4 * 16 * 8, n->sms), 256, 0, n->stream>>>(n->params, n->wu, n->wdu, n->w5u);
     NCK(n, cudaGetLastError());
     return LBM_ACE_OK;
 }
@@ -944,24 +1247,39 @@ int lbm_ace_net_create(int device, void* stream, lbm_ace_net** out)
     CREATE_CK(cudaMalloc(&n->adam_m, NPARAM * sizeof(float)));
     CREATE_CK(cudaMalloc(&n->adam_v, NPARAM * sizeof(float)));
     CREATE_CK(cudaMalloc(&n->grad, NPARAM * sizeof(float)));
-    CREATE_CK(cudaMalloc(&n->wf, 3 * 9 * C * C * sizeof(bf16)));
-    CREATE_CK(cudaMalloc(&n->wd, 3 * 9 * C * C * sizeof(bf16)));
+    CREATE_CK(cudaMalloc(&n->wu, 3 * 9 * C * C * sizeof(bf16)));
+    CREATE_CK(cudaMalloc(&n->wdu, 3 * 9 * C * C * sizeof(bf16)));
+    CREATE_CK(cudaMalloc(&n->w5u, 9 * 4 * 16 * 8 * sizeof(bf16)));
+    CREATE_CK(cudaMalloc(&n->derr, sizeof(int)));
+    CREATE_CK(cudaMemset(n->derr, 0, sizeof(int)));
     CREATE_CK(cudaMemset(n->params, 0, NPARAM * sizeof(float)));
     CREATE_CK(cudaMemset(n->adam_m, 0, NPARAM * sizeof(float)));
     CREATE_CK(cudaMemset(n->adam_v, 0, NPARAM * sizeof(float)));
     CREATE_CK(cudaMemset(n->grad, 0, NPARAM * sizeof(float)));
-    CREATE_CK(cudaMemset(n->wf, 0, 3 * 9 * C * C * sizeof(bf16)));
-    CREATE_CK(cudaMemset(n->wd, 0, 3 * 9 * C * C * sizeof(bf16)));
+    CREATE_CK(cudaMemset(n->wu, 0, 3 * 9 * C * C * sizeof(bf16)));
+    CREATE_CK(cudaMemset(n->wdu, 0, 3 * 9 * C * C * sizeof(bf16)));
+    CREATE_CK(cudaMemset(n->w5u, 0, 9 * 4 * 16 * 8 * sizeof(bf16)));
     // launch shapes: persistent grids of resident CTAs
-    n->conv_smem = (size_t)(W_SMEM + 2 * HPX * PS) * sizeof(bf16);
+    n->conv_smem = umma_smem_bytes<32>();
+    n->out_smem = umma_smem_bytes<16>();
     n->wg_smem = (size_t)(TH * TW * PS + HPX * PS) * sizeof(bf16);
     n->ob_smem = (size_t)HPX * PS * sizeof(bf16);
-    CREATE_CK(cudaFuncSetAttribute(surr_conv_mma<MODE_FWD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)n->conv_smem));
-    CREATE_CK(cudaFuncSetAttribute(surr_conv_mma<MODE_DGRAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)n->conv_smem));
+    CREATE_CK(cudaFuncSetAttribute(surr_conv_umma<MODE_FWD, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)n->conv_smem));
+    CREATE_CK(cudaFuncSetAttribute(surr_conv_umma<MODE_DGRAD, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)n->conv_smem));
+    CREATE_CK(cudaFuncSetAttribute(surr_conv_umma<MODE_OUT, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)n->out_smem));
+    // the persistent tensor-core kernels want all of the unified L1/shared storage as shared memory
+    CREATE_CK(cudaFuncSetAttribute(surr_conv_umma<MODE_FWD, 32>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    CREATE_CK(cudaFuncSetAttribute(surr_conv_umma<MODE_DGRAD, 32>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    CREATE_CK(cudaFuncSetAttribute(surr_conv_umma<MODE_OUT, 16>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     CREATE_CK(cudaFuncSetAttribute(surr_wgrad_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)n->wg_smem));
     int occ = 0;
-    CREATE_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, surr_conv_mma<MODE_FWD>, CONV_THREADS, n->conv_smem));
-    n->conv_grid = std::max(1, occ) * n->sms;
+    // persistent, one CTA per SM (the occupancy the runtime reports for tcgen05 kernels)
+    CREATE_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, surr_conv_umma<MODE_FWD, 32>, UMMA_THREADS, n->conv_smem));
+    n->conv_occ = occ;
+    n->conv_grid = n->sms;
+    CREATE_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, surr_conv_umma<MODE_OUT, 16>, UMMA_THREADS, n->out_smem));
+    n->out_occ = occ;
+    n->out_grid = n->sms;
     CREATE_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, surr_wgrad_mma, WG_THREADS, n->wg_smem));
     n->wg_grid = std::max(1, occ) * n->sms;
     CREATE_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, surr_out_bwd, 256, n->ob_smem));
@@ -1014,7 +1332,7 @@ int lbm_ace_net_forward(lbm_ace_net* n, const float* phi, const float* u, const 
     int rc = check_dims(n, batch, ny, nx);
     if (rc) return rc;
     NetDevice gd(n->dev);
-    rc = ensure_acts(n, (long long)batch * ny * nx, batch);
+    rc = ensure_acts(n, (long long)batch * ny * nx, batch, ny, nx);
     if (rc) return rc;
     return run_forward(n, phi, u, v, phi_out, batch, ny, nx, false);
 }
@@ -1029,7 +1347,7 @@ int lbm_ace_net_loss_grad(lbm_ace_net* n, const float* phi, const float* u, cons
     if (rc) return rc;
     NetDevice gd(n->dev);
     const long long P = (long long)batch * ny * nx;
-    rc = ensure_acts(n, P, batch);
+    rc = ensure_acts(n, P, batch, ny, nx);
     if (rc) return rc;
     rc = run_forward(n, phi, u, v, n->outb, batch, ny, nx, true);
     if (rc) return rc;
@@ -1041,22 +1359,24 @@ int lbm_ace_net_loss_grad(lbm_ace_net* n, const float* phi, const float* u, cons
     // layer 5
     const int gob = (int)std::min<long long>(g.ntiles, n->ob_grid);
     surr_out_bwd<<<gob, 256, n->ob_smem, n->stream>>>(n->a[3], n->z[3], n->gz5, n->params, n->gzb[0], n->wpart, g);
-    surr_reduce<<<grid1(L5_N, n->sms), 256, 0, n->stream>>>(n->wpart, gob, L5_N, L5_N, n->grad + OFF_W5);
+    surr_reduce<<<(L5_N + 31) / 32, 256, 0, n->stream>>>(n->wpart, gob, L5_N, L5_N, n->grad + OFF_W5);
     // layers 4, 3, 2: weight gradient, then dL/dz of the layer below
     const int gwg = (int)std::min<long long>(g.ntiles, n->wg_grid);
-    const int gcv = (int)std::min<long long>(g.ntiles, n->conv_grid);
+    const UGeo ug = make_ugeo(batch, ny, nx);
+    const int gcv = (int)std::min<long long>(ug.ntiles, n->conv_grid);
     int cur = 0;
     for (int l = 2; l >= 0; --l) { // hidden layer l + 2 (1-based), input a[l], output gz of z[l]
         surr_wgrad_mma<<<gwg, WG_THREADS, n->wg_smem, n->stream>>>(n->gzb[cur], n->a[l], n->wpart, g);
-        surr_reduce<<<grid1(LH_N, n->sms), 256, 0, n->stream>>>(n->wpart, gwg, LH_N, LH_N, n->grad + OFF_W2 + l * LH_N);
-        surr_conv_mma<MODE_DGRAD><<<gcv, CONV_THREADS, n->conv_smem, n->stream>>>(
-            n->gzb[cur], n->wd + (size_t)l * 9 * C * C, nullptr, n->z[l], nullptr, n->gzb[cur ^ 1], g);
+        surr_reduce<<<(LH_N + 31) / 32, 256, 0, n->stream>>>(n->wpart, gwg, LH_N, LH_N, n->grad + OFF_W2 + l * LH_N);
+        surr_conv_umma<MODE_DGRAD, 32><<<gcv, UMMA_THREADS, n->conv_smem, n->stream>>>(
+            n->gzb[cur], n->wdu + (size_t)l * 9 * C * C, nullptr, n->z[l], nullptr, n->gzb[cur ^ 1], nullptr, nullptr,
+            ug, n->derr);
         cur ^= 1;
     }
     // layer 1
     const int giw = (int)std::min<long long>(g.ntiles, n->iw_grid);
     surr_in_wgrad<<<giw, 256, 0, n->stream>>>(n->gzb[cur], phi, u, v, n->wpart, g);
-    surr_reduce<<<grid1(L1_N, n->sms), 256, 0, n->stream>>>(n->wpart, giw, L1_N, L1_N, n->grad + OFF_W1);
+    surr_reduce<<<(L1_N + 31) / 32, 256, 0, n->stream>>>(n->wpart, giw, L1_N, L1_N, n->grad + OFF_W1);
     NCK(n, cudaGetLastError());
     n->have_grad = true;
     if (loss) {
@@ -1067,6 +1387,8 @@ int lbm_ace_net_loss_grad(lbm_ace_net* n, const float* phi, const float* u, cons
         double s = 0.0;
         for (size_t k = 0; k < np; ++k) s += n->hpart[k];
         *loss = s / (double)P;
+        rc = check_err(n);
+        if (rc) return rc;
         if (!std::isfinite(*loss)) return nfail(n, LBM_ACE_ENUMERIC, "loss is not finite (%g)", *loss);
     }
     if (grad) {
@@ -1137,6 +1459,18 @@ int lbm_ace_net_synchronize(lbm_ace_net* n)
     if (!n) return nfail(nullptr, LBM_ACE_EINVAL, "net is NULL");
     NetDevice gd(n->dev);
     NCK(n, cudaStreamSynchronize(n->stream));
+    return check_err(n);
+}
+
+int lbm_ace_net_launch_shape(const lbm_ace_net* n, int* conv_ctas, int* conv_occupancy, int* out_ctas,
+                             int* out_occupancy, int* sms)
+{
+    if (!n) return nfail(nullptr, LBM_ACE_EINVAL, "net is NULL");
+    if (conv_ctas) *conv_ctas = n->conv_grid;
+    if (conv_occupancy) *conv_occupancy = n->conv_occ;
+    if (out_ctas) *out_ctas = n->out_grid;
+    if (out_occupancy) *out_occupancy = n->out_occ;
+    if (sms) *sms = n->sms;
     return LBM_ACE_OK;
 }
 
@@ -1148,9 +1482,10 @@ void lbm_ace_net_destroy(lbm_ace_net* n)
     NetDevice gd(n->dev);
     if (n->stream) cudaStreamSynchronize(n->stream); else cudaDeviceSynchronize();
     free_acts(n);
-    void* bufs[] = {n->params, n->adam_m, n->adam_v, n->grad, n->wf, n->wd, n->rpart, n->rpart2, n->wpart,
-                    n->hyb[0], n->hyb[1], n->hyb[2], n->hyb[3]};
+    void* bufs[] = {n->params, n->adam_m, n->adam_v, n->grad, n->wu, n->wdu, n->w5u, n->derr, n->tsum,
+                    n->rpart, n->rpart2, n->wpart, n->hyb_part};
     for (void* p : bufs) cudaFree(p);
+    for (float* p : n->hyb) cudaFree(p);
     delete n;
 }
 
@@ -1172,57 +1507,84 @@ int lbm_ace_hybrid_advance(lbm_ace_ctx* lat, lbm_ace_net* n, long long windows, 
     const int nx = P.nx, ny = P.ny;
     const long long N = (long long)nx * ny;
     NetDevice gd(n->dev);
-    rc = ensure_acts(n, N, 1);
+    rc = ensure_acts(n, N, 1, ny, nx);
     if (rc) return rc;
+    constexpr int NB = HYB_DEPTH + 1;
     if (n->hyb_n < N) {
-        for (int k = 0; k < 4; ++k) { cudaFree(n->hyb[k]); n->hyb[k] = nullptr; }
+        for (float*& p : n->hyb) { cudaFree(p); p = nullptr; }
         n->hyb_n = 0;
-        for (int k = 0; k < 4; ++k) NCK(n, cudaMalloc(&n->hyb[k], (size_t)N * sizeof(float)));
+        for (float*& p : n->hyb) NCK(n, cudaMalloc(&p, (size_t)N * sizeof(float)));
         n->hyb_n = N;
     }
-    float* cur = n->hyb[0];
-    float* cand = n->hyb[1];
-    float* u = n->hyb[2];
-    float* v = n->hyb[3];
+    if (!n->hyb_part) NCK(n, cudaMalloc(&n->hyb_part, (size_t)HYB_DEPTH * 3 * RED_BLOCKS * sizeof(double)));
+    float* ring[NB];
+    for (int k = 0; k < NB; ++k) ring[k] = n->hyb[k];
+    float* u = n->hyb[NB];
+    float* v = n->hyb[NB + 1];
+    const int rb = red_blocks(ny, nx);
 #define LAT(call) do { const int r_ = (call); if (r_) return nfail(n, r_, "lattice: %s", lbm_ace_last_error(lat)); } while (0)
     lbm_ace_hybrid_stats st;
     std::memset(&st, 0, sizeof st);
     long long t = lbm_ace_steps_done(lat);
-    LAT(lbm_ace_get_phi_device(lat, cur));
-    rc = lbm_ace_net_metrics(n, cur, ny, nx, &st.mass0, &st.width0);
+    int c = 0; // ring index of the current field
+    LAT(lbm_ace_get_phi_device(lat, ring[c]));
+    rc = lbm_ace_net_metrics(n, ring[c], ny, nx, &st.mass0, &st.width0);
     if (rc) return rc;
-    bool stale = false; // the lattice lags behind cur (surrogate windows since its last step)
+    bool stale = false; // the lattice lags behind ring[c] (surrogate windows since its last step)
     const int K = LBM_ACE_NET_K;
-    for (long long w = 0; w < windows; ++w) {
-        LAT(lbm_ace_velocity_device(lat, (double)t + 0.5 * K, u, v));
-        rc = run_forward(n, cur, u, v, cand, 1, ny, nx, false);
-        if (rc) return rc;
-        double m = 0.0, wd = 0.0;
-        rc = lbm_ace_net_metrics(n, cand, ny, nx, &m, &wd);
-        if (rc && rc != LBM_ACE_ENUMERIC) return rc;
-        const double dm = st.mass0 != 0.0 ? std::fabs(m - st.mass0) / std::fabs(st.mass0) : std::fabs(m);
-        const double dw = st.width0 > 0.0 ? std::fabs(wd - st.width0) / st.width0 : (wd == 0.0 ? 0.0 : INFINITY);
-        if (rc == LBM_ACE_OK && dm <= mass_tol && dw <= width_tol) {
-            std::swap(cur, cand);
-            stale = true;
-            st.surrogate_windows += 1;
+    std::vector<double> hp((size_t)HYB_DEPTH * 3 * rb);
+    long long w = 0;
+    while (w < windows) {
+        // up to HYB_DEPTH surrogate windows back to back, each field in the next ring slot,
+        // with its checks reduced on the device; one synchronisation for the batch
+        const int depth = (int)std::min<long long>(HYB_DEPTH, windows - w);
+        for (int j = 0; j < depth; ++j) {
+            LAT(lbm_ace_velocity_device(lat, (double)(t + (long long)j * K) + 0.5 * K, u, v));
+            rc = run_forward(n, ring[(c + j) % NB], u, v, ring[(c + j + 1) % NB], 1, ny, nx, false);
+            if (rc) return rc;
+            surr_metrics<<<rb, 256, 0, n->stream>>>(ring[(c + j + 1) % NB], ny, nx, n->hyb_part + (size_t)j * 3 * rb);
+        }
+        NCK(n, cudaGetLastError());
+        NCK(n, cudaMemcpyAsync(hp.data(), n->hyb_part, (size_t)depth * 3 * rb * sizeof(double), cudaMemcpyDeviceToHost,
+                               n->stream));
+        NCK(n, cudaStreamSynchronize(n->stream));
+        int acc = 0; // windows accepted, in order, before the first that fails a check
+        for (; acc < depth; ++acc) {
+            double q[3] = {0.0, 0.0, 0.0};
+            for (int m = 0; m < 3; ++m)
+                for (int k = 0; k < rb; ++k) q[m] += hp[((size_t)acc * 3 + m) * rb + k];
+            const double mass = q[0], width = q[2] > 0.0 ? q[1] / q[2] : 0.0;
+            if (!std::isfinite(q[0]) || !std::isfinite(q[1]) || !std::isfinite(q[2])) break;
+            const double dm = st.mass0 != 0.0 ? std::fabs(mass - st.mass0) / std::fabs(st.mass0) : std::fabs(mass);
+            const double dw = st.width0 > 0.0 ? std::fabs(width - st.width0) / st.width0 : (width == 0.0 ? 0.0 : INFINITY);
+            if (!(dm <= mass_tol && dw <= width_tol)) break;
             st.max_mass_drift = std::max(st.max_mass_drift, dm);
             st.max_width_dev = std::max(st.max_width_dev, dw);
-        } else {
-            if (stale) LAT(lbm_ace_reset_device(lat, cur, t));
-            LAT(lbm_ace_step(lat, K));
-            LAT(lbm_ace_get_phi_device(lat, cur));
-            stale = false;
-            st.fallback_windows += 1;
         }
-        t += K;
-        st.windows += 1;
+        if (acc > 0) {
+            c = (c + acc) % NB;
+            t += (long long)acc * K;
+            stale = true;
+            st.surrogate_windows += acc;
+            st.windows += acc;
+            w += acc;
+        }
+        if (acc < depth) { // the first rejected window: K lattice Boltzmann steps from ring[c]
+            if (stale) LAT(lbm_ace_reset_device(lat, ring[c], t));
+            LAT(lbm_ace_step(lat, K));
+            LAT(lbm_ace_get_phi_device(lat, ring[c]));
+            stale = false;
+            t += K;
+            st.fallback_windows += 1;
+            st.windows += 1;
+            w += 1;
+        }
     }
-    if (stale) LAT(lbm_ace_reset_device(lat, cur, t));
+    if (stale) LAT(lbm_ace_reset_device(lat, ring[c], t));
     LAT(lbm_ace_synchronize(lat));
 #undef LAT
-    n->hyb[0] = cur;
-    n->hyb[1] = cand;
+    rc = check_err(n);
+    if (rc) return rc;
     if (stats) *stats = st;
     return LBM_ACE_OK;
 }

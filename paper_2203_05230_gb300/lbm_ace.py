@@ -47,6 +47,7 @@ EXPORTS = (
     "lbm_ace_net_create", "lbm_ace_net_set_params", "lbm_ace_net_get_params", "lbm_ace_net_forward",
     "lbm_ace_net_loss_grad", "lbm_ace_net_adam", "lbm_ace_net_gather", "lbm_ace_net_metrics",
     "lbm_ace_net_synchronize", "lbm_ace_net_last_error", "lbm_ace_net_destroy", "lbm_ace_hybrid_advance",
+    "lbm_ace_net_launch_shape",
 )
 NET_WIDTH, NET_K, NET_PARAMS = 32, 16, 28929
 NOALLOC_CHUNK = 65536
@@ -167,6 +168,8 @@ def load(build_if_missing: bool = True):
     L.lbm_ace_net_gather.argtypes = [_P, _P, _P, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int, ctypes.c_longlong]
     L.lbm_ace_net_metrics.argtypes = [_P, _P, ctypes.c_int, ctypes.c_int, _D, _D]
     L.lbm_ace_net_synchronize.argtypes = [_P]
+    L.lbm_ace_net_launch_shape.argtypes = [_P] + [ctypes.POINTER(ctypes.c_int)] * 5
+    L.lbm_ace_net_launch_shape.restype = ctypes.c_int
     L.lbm_ace_net_last_error.argtypes = [_P]
     L.lbm_ace_net_last_error.restype = ctypes.c_char_p
     L.lbm_ace_net_destroy.argtypes = [_P]
@@ -510,6 +513,13 @@ class Net:
         return m.value, w.value
 
     metrics = lbm_ace_net_metrics
+
+    def lbm_ace_net_launch_shape(self) -> dict:
+        v = [ctypes.c_int() for _ in range(5)]
+        self._check(self._lib.lbm_ace_net_launch_shape(self.h, *[ctypes.byref(x) for x in v]))
+        return dict(zip(("conv_ctas", "conv_occupancy", "out_ctas", "out_occupancy", "sms"), (x.value for x in v)))
+
+    launch_shape = lbm_ace_net_launch_shape
 
     def lbm_ace_net_synchronize(self) -> None:
         self._check(self._lib.lbm_ace_net_synchronize(self.h))
