@@ -12,6 +12,13 @@ Prints one JSON line. ``--impl reference`` times the FP64 CPU oracle instead (on
 the host cores, a bounded sample per step). Under torchrun each rank runs an
 independent replica of the workload on its own GPU (no collective on the data
 path); the line reports the aggregate over ranks.
+
+``--surrogate`` measures the learned surrogate instead (one GPU): the forward pass on a
+batch of 256 x 256 images (CUDA events, the tensor-core roofline of its algorithmic
+FLOPs), and, after training it on GPU-generated pairs, one period of the 256 x 256
+single vortex advanced by the hybrid (surrogate windows of 16 steps with the lattice
+Boltzmann fallback) against the plain FP32 lattice Boltzmann run: wall-clock MLUPS of
+both and the phi-L2 error between them.
 """
 from __future__ import annotations
 
@@ -50,6 +57,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--surrogate", action="store_true", help="benchmark the learned surrogate instead")
+    ap.add_argument("--surr-batch", type=int, default=16, help="images per timed forward (surrogate mode)")
+    ap.add_argument("--surr-traj", type=int, default=625,
+                    help="training trajectories of 32 windows (surrogate mode; 0: forward timing only)")
+    ap.add_argument("--surr-train-steps", type=int, default=6000)
     return ap.parse_args()
 
 
@@ -343,10 +355,112 @@ def run_e2e(args, v, prec, stream, dev, A):
                     "bytes per step are the run's totals / K"}
 
 
+SURR_FLOP_PER_PIXEL = 2 * 9 * (3 * 32 + 3 * 32 * 32 + 32)   # multiply-adds of the five layers x 2
+
+
+def measured_bf16_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["bf16_tflops"]), "measured (MEASURED_PEAKS.json bf16_tflops, burst)"
+    return 1900.0, "fallback"
+
+
+def run_surrogate(args):
+    """Forward throughput of the learned surrogate and the hybrid vortex rollout."""
+    import torch
+    torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    from paper_2203_05230_gb300 import lbm_ace as A
+    from paper_2203_05230_gb300 import surrogate as SG
+    from paper_2203_05230_gb300 import workloads as W
+    stream = torch.cuda.current_stream()
+    steps = 400 if args.steps == 20000 else args.steps
+    L, B = W.SURROGATE_TILE, args.surr_batch
+    net = A.Net(dev, stream)
+    net.set_params(W.surrogate_init_params(seed=0))
+    g = torch.Generator(device="cuda").manual_seed(0)
+    phi = torch.rand((B, L, L), device="cuda", generator=g)
+    u = (torch.rand((B, L, L), device="cuda", generator=g) - 0.5) * 0.1
+    v = (torch.rand((B, L, L), device="cuda", generator=g) - 0.5) * 0.1
+    out = torch.empty_like(phi)
+    for _ in range(args.warmup):
+        net.forward(phi, u, v, out, B, L, L)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev) as cs:
+        e0.record(stream)
+        for _ in range(steps):
+            net.forward(phi, u, v, out, B, L, L)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    clk = cs.summary()
+    fwd = e0.elapsed_time(e1) / 1e3 / steps
+    flops = SURR_FLOP_PER_PIXEL * B * L * L
+    peak, peak_kind = measured_bf16_peak()
+    achieved = flops / fwd / 1e12
+    line = {"metric": "MLUPS", "value": None, "unit": "MLUPS", "n_gpus": 1, "steps": steps, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16 (fp32 accumulate)",
+            "data": "synthetic",
+            "config": {"workload": f"learned surrogate of 16 LB steps: forward on {B} x {L}^2 images; hybrid rollout "
+                                   f"of one period of the {L}^2 single vortex (eps 1, tau 0.8, U0 0.04, T 4096)",
+                       "network": "5 x periodic 3x3 conv, 3-32-32-32-32-1, GELU, mass-conserving residual",
+                       "parallelism": "single GPU",
+                       "l2": "forward activations of the timed batch exceed L2 (5 x 64 MB BF16 at batch 16)"},
+            "forward": {"ms": fwd * 1e3, "images": B, "lup_equivalent_mlups": B * L * L * 16 / fwd / 1e6},
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                         "algorithmic_flop_per_launch": flops, "kernel": "whole forward (5 launches + residual)",
+                         "note": "the GELU epilogue on the FP32 units bounds the narrow layers, not the tensor pipe"},
+            "clocks": clk, "gpu_launches": 6 * steps}
+    if args.surr_traj > 0:
+        data = SG.generate(args.surr_traj, 32, L=L, seed=0, stream=stream)
+        held = max(1, args.surr_traj // 25)
+        n_train = (args.surr_traj - held) * 32
+        tr = SG.Trainer(net, data, batch=16, seed=0)
+        t0 = time.perf_counter()
+        tr.train(args.surr_train_steps, train_pairs=np.arange(n_train))
+        train_s = time.perf_counter() - t0
+        ev = tr.evaluate(np.arange(n_train, data.n_pairs))
+        del data
+        ro = SG.vortex_rollout(net, L=L, stream=stream)
+        lups = L * L * ro["T"]
+        line["value"] = lups / ro["hybrid_seconds"] / 1e6   # wall clock of the period on a built lattice
+        steps_w = ro["windows"]
+        line["e2e"] = {"value": lups / ro["hybrid_e2e_seconds"] / 1e6, "unit": "MLUPS",
+                       "h2d_bytes_per_step": 8 * L * L / steps_w, "d2h_bytes_per_step": 8 * L * L / steps_w,
+                       "what": "lattice built from the host phi0 (FP64), one period by the hybrid, phi read back to "
+                               "the host, wall clock; a step is one window of 16 LB steps, bytes are the run's "
+                               "totals per window"}
+        line["vs_plain_fp32_lbm"] = {"mlups_plain": lups / ro["lbm_seconds"] / 1e6, "speedup": ro["speedup"],
+                                     "phi_l2_vs_plain_at_T": ro["E2_vs_lbm_T"],
+                                     "phi_l2_vs_plain_at_T_half": ro["E2_vs_lbm_half"],
+                                     "surrogate_windows": ro["surrogate_windows"],
+                                     "fallback_windows": ro["fallback_windows"],
+                                     "mass_drift": ro["mass_drift_hybrid"]}
+        line["training"] = {"pairs": args.surr_traj * 32, "adam_steps": args.surr_train_steps, "seconds": train_s,
+                            "held_out_phi_l2": ev["E2_net"], "persistence_phi_l2": ev["E2_persistence"]}
+    net.close()
+    if not args.no_cpu_baseline:
+        from oracle import surrogate as S
+        rng = np.random.default_rng(0)
+        p0 = rng.uniform(0, 1, (1, L, L))
+        t0 = time.perf_counter()
+        S.forward(W.surrogate_init_params(seed=0), p0, p0 * 0.05, p0 * 0.05)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": L * L * 16 / dt / 1e6, "unit": "MLUPS", "cores": os.cpu_count(),
+                                "kind": "oracle", "sample": f"one FP64 oracle forward of one {L}^2 image "
+                                                            "(numpy, LB-step equivalents of 16 per pixel)"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.surrogate:
+        return run_surrogate(args)
     return run_ours(args)
 
 

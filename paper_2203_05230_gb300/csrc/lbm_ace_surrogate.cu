@@ -734,21 +734,32 @@ __device__ __forceinline__ double warp_sum_ordered(const double* v, int n)
     return s;
 }
 
+// Deterministic block-wide sum of n doubles: thread i sums v[i], v[i + 256], ... in order,
+// then a fixed tree over the 256 thread sums. Valid in thread 0; blockDim.x must be 256.
+__device__ __forceinline__ double block_sum_ordered(const double* v, int n, double* red)
+{
+    double s = 0.0;
+    for (int k = threadIdx.x; k < n; k += 256) s += v[k];
+    red[threadIdx.x] = s;
+    __syncthreads();
+#pragma unroll
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    return red[0];
+}
+
 // phi_out = phi + (z_5 - mean(z_5)) per image; tsum holds partial sums of z_5, those of
 // image b being [b * tpi, (b + 1) * tpi).
 __global__ void __launch_bounds__(256) surr_residual(const float* __restrict__ phi, const float* __restrict__ z5,
                                                      const double* __restrict__ tsum, int tpi,
                                                      float* __restrict__ out, int H, int W)
 {
-    __shared__ double mean;
+    __shared__ double red[256];
     const int b = blockIdx.y;
     const long long HWn = (long long)H * W;
-    if (threadIdx.x < 32) {
-        const double s = warp_sum_ordered(tsum + (size_t)b * tpi, tpi);
-        if (threadIdx.x == 0) mean = s / (double)HWn;
-    }
-    __syncthreads();
-    const double m = mean;
+    const double m = block_sum_ordered(tsum + (size_t)b * tpi, tpi, red) / (double)HWn;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < HWn; q += (long long)gridDim.x * blockDim.x) {
         const size_t k = (size_t)b * HWn + q;
         out[k] = (float)((double)phi[k] + ((double)z5[k] - m));

@@ -174,6 +174,14 @@ def vortex_rollout(net: A.Net, L: int = 256, eps: float = 1.0, tau: float = 0.8,
         g.synchronize()
         res["hybrid_seconds"] = time.perf_counter() - t0
     res["speedup"] = res["lbm_seconds"] / res["hybrid_seconds"]
+    # end to end through the public API: lattice built from the host phi0, the period,
+    # phi read back to the host
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    with A.Lattice(**kw) as g:
+        net.hybrid_advance(g, windows, mass_tol, width_tol)
+        g.phi()
+    res["hybrid_e2e_seconds"] = time.perf_counter() - t0
 
     def e2(a, b):
         return math.sqrt(((a - b) ** 2).sum() / (b ** 2).sum())
