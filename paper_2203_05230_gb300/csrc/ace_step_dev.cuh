@@ -73,6 +73,9 @@ __global__ void __launch_bounds__(PAIR_THREADS, 4) ace_step_dev(const DevArgs<S>
     using C = Dev16<S>;
     __shared__ __align__(16) float chi_s[4][PAIR_COLS + 4]; // index j holds column x0 + j - 2
     __shared__ double red_s[PAIR_THREADS / 32];
+    // programmatic dependent launch (no-ops for an ordinary launch): see ace_step_pair
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
 
     const int tx = threadIdx.x;
     const int lane = tx & 31;

@@ -216,6 +216,11 @@ __global__ void __launch_bounds__(PAIR_THREADS, sizeof(T) == 4 ? 5 : 1) ace_step
 {
     __shared__ __align__(16) T chi_s[4][PAIR_COLS + 4];
     __shared__ double red_s[PAIR_THREADS / 32];
+    // Programmatic dependent launch: let the next step's CTAs be scheduled as slots free
+    // up, and wait for the previous step (all of its memory) before touching the state.
+    // Both are no-ops for an ordinary launch.
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
     pair_tile<T, MODEL>(a, vel, blockIdx.x * PAIR_COLS, blockIdx.y * a.rows, chi_s, red_s,
                         &a.mass_part[(long long)blockIdx.y * gridDim.x + blockIdx.x]);
 }

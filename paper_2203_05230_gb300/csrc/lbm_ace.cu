@@ -18,6 +18,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <utility>
 #include <vector>
 
 using namespace lbmace;
@@ -148,6 +149,24 @@ VelPlanes<T> planes(lbm_ace_ctx* c)
 constexpr int BULK_TX = 128;
 constexpr int BULK_STAGES = 6;
 
+// Launch with programmatic stream serialisation: the kernel may start while the previous
+// kernel in the stream drains; it waits (griddepcontrol.wait) before reading the state.
+template <typename... KArgs, typename... Args>
+void launch_pdl(void (*kernel)(KArgs...), dim3 grid, int threads, cudaStream_t stream, Args&&... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 template <typename T, int MODEL, class Vel>
 void launch_step_k(lbm_ace_ctx* c, const Vel& vel)
 {
@@ -158,7 +177,7 @@ void launch_step_k(lbm_ace_ctx* c, const Vel& vel)
     else if (c->variant == 3)
         ace_step_warp<T, MODEL, Vel><<<grid, TILE_X, 0, c->stream>>>(make_args<T>(c), vel);
     else if (c->variant == 4)
-        ace_step_pair<T, MODEL, Vel><<<grid, PAIR_THREADS, 0, c->stream>>>(make_args<T>(c), vel);
+        launch_pdl(ace_step_pair<T, MODEL, Vel>, grid, PAIR_THREADS, c->stream, make_args<T>(c), vel);
     else
         ace_step<T, MODEL, Vel><<<grid, TILE_X, 0, c->stream>>>(make_args<T>(c), vel);
 }
@@ -200,7 +219,7 @@ void launch_dev_k(lbm_ace_ctx* c, const Vel& vel)
 {
     dim3 grid(c->grid_x, c->grid_y);
     StepArgs<float> a = make_args<float>(c);
-    ace_step_dev<S, MODEL, Vel><<<grid, PAIR_THREADS, 0, c->stream>>>(make_dev<S>(c), a, vel);
+    launch_pdl(ace_step_dev<S, MODEL, Vel>, grid, PAIR_THREADS, c->stream, make_dev<S>(c), a, vel);
 }
 
 template <typename S, int MODEL>
