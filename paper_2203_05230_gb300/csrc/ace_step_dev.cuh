@@ -68,7 +68,7 @@ struct DevArgs {
 };
 
 template <typename S, int MODEL, class Vel>
-__global__ void __launch_bounds__(PAIR_THREADS, 4) ace_step_dev(const DevArgs<S> d, const StepArgs<float> a, const Vel vel)
+__global__ void __launch_bounds__(PAIR_THREADS, 5) ace_step_dev(const DevArgs<S> d, const StepArgs<float> a, const Vel vel)
 {
     using C = Dev16<S>;
     __shared__ __align__(16) float chi_s[4][PAIR_COLS + 4]; // index j holds column x0 + j - 2
