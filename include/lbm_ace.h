@@ -124,7 +124,10 @@ typedef struct lbm_ace_params {
                             memory by bulk copies (needs nx * element size a multiple of
                             16 bytes), 3 = independent 32-column warps with loads issued a
                             row ahead, 4 = two columns per thread with paired loads and
-                            stores (needs an even nx). All give bit-identical results.
+                            stores (needs an even nx), 6 = two steps per launch with the
+                            intermediate populations in shared memory (FP32, even nx, no
+                            velocity callback; an odd step count ends with one variant-4
+                            step; keeps a second phi plane). All give bit-identical results.
                             The 16-bit deviation storage has its own kernel (reported as 5)
                             and takes 0 here. */
 } lbm_ace_params;

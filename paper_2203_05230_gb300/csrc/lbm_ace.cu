@@ -9,6 +9,7 @@
 #include "ace_step_warp.cuh"
 #include "ace_step_pair.cuh"
 #include "ace_step_dev.cuh"
+#include "ace_step_tb2.cuh"
 
 #include <cuda_runtime.h>
 
@@ -50,6 +51,7 @@ struct lbm_ace_ctx {
     void* f[2] = {nullptr, nullptr};
     int cur = 0;            // buffer holding f*(t-1)
     void* phi = nullptr;    // phi(t-1) plane (deviation storage: phi2[pcur])
+    void* phi_alt = nullptr; // second FP32 phi plane of the two-step kernel (variant 6)
     float* phi2[2] = {nullptr, nullptr}; // deviation storage: ping-pong FP32 phi planes
     int pcur = 0;
     double* step_part = nullptr; int n_step_part = 0;
@@ -176,7 +178,7 @@ void launch_step_k(lbm_ace_ctx* c, const Vel& vel)
             <<<grid, BULK_TX, c->smem, c->stream>>>(make_args<T>(c), vel, c->dev_err);
     else if (c->variant == 3)
         ace_step_warp<T, MODEL, Vel><<<grid, TILE_X, 0, c->stream>>>(make_args<T>(c), vel);
-    else if (c->variant == 4)
+    else if (c->variant == 4 || c->variant == 6) // variant 6: a lone step (odd count) is one pair step
         launch_pdl(ace_step_pair<T, MODEL, Vel>, grid, PAIR_THREADS, c->stream, make_args<T>(c), vel);
     else
         ace_step<T, MODEL, Vel><<<grid, TILE_X, 0, c->stream>>>(make_args<T>(c), vel);
@@ -241,6 +243,50 @@ void launch_dev_s(lbm_ace_ctx* c)
 {
     if (c->p.model == LBM_ACE_MODEL_MODIFIED) launch_dev_m<S, MODEL_MODIFIED>(c);
     else launch_dev_m<S, MODEL_CONSERVATIVE>(c);
+}
+
+// Two steps t -> t + 2 in one launch (variant 6, FP32): reads f[cur] and phi, writes
+// f[1 - cur] and phi_alt.
+template <int MODEL, class Vel>
+void launch_tb2_k(lbm_ace_ctx* c, const Vel& va, const Vel& vb)
+{
+    StepArgs<float> a = make_args<float>(c);
+    StepArgs<float> b = a;
+    b.phi = (float*)c->phi_alt;
+    b.first = 0;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(c->grid_x, c->grid_y);
+    cfg.blockDim = dim3(TB_THREADS);
+    cfg.dynamicSmemBytes = c->smem;
+    cfg.stream = c->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, ace_step_tb2<MODEL, Vel>, a, b, va, vb);
+}
+
+template <int MODEL>
+void launch_tb2_m(lbm_ace_ctx* c)
+{
+    switch (c->p.velocity_kind) {
+    case LBM_ACE_VEL_SINGLE_VORTEX:
+        launch_tb2_k<MODEL>(c, vortex<float>(c, (double)c->t), vortex<float>(c, (double)c->t + 1.0));
+        break;
+    case LBM_ACE_VEL_UNIFORM: {
+        VelUniform<float> v; v.ux = float(c->p.ux); v.uy = float(c->p.uy);
+        launch_tb2_k<MODEL>(c, v, v);
+        break;
+    }
+    default: launch_tb2_k<MODEL>(c, planes<float>(c), planes<float>(c)); break;
+    }
+}
+
+void launch_tb2_any(lbm_ace_ctx* c)
+{
+    if (c->p.model == LBM_ACE_MODEL_MODIFIED) launch_tb2_m<MODEL_MODIFIED>(c);
+    else launch_tb2_m<MODEL_CONSERVATIVE>(c);
 }
 
 void launch_step_any(lbm_ace_ctx* c)
@@ -342,6 +388,16 @@ int occupancy_k(lbm_ace_ctx* c, int* blocks)
         c->smem = 0;
         c->tile_x = PAIR_COLS;
         CK(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, ace_step_pair<T, MODEL, Vel>, PAIR_THREADS, 0));
+    } else if (c->variant == 6) {
+        if constexpr (sizeof(T) == 4) {
+            auto k = ace_step_tb2<MODEL, Vel>;
+            c->smem = sizeof(TbSmem);
+            c->tile_x = TB_COLS;
+            CK(c, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem));
+            CK(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k, TB_THREADS, c->smem));
+        } else {
+            return fail(c, LBM_ACE_EINVAL, "kernel_variant 6 is FP32 only");
+        }
     } else {
         c->smem = 0;
         c->tile_x = TILE_X;
@@ -546,7 +602,7 @@ void lbm_ace_destroy(lbm_ace_ctx* c)
     if (!c) return;
     DeviceGuard g(c->dev);
     if (c->stream) cudaStreamSynchronize(c->stream); else cudaDeviceSynchronize();
-    void* bufs[] = {c->f[0], c->f[1], c->phi, c->phi2[0], c->phi2[1], c->step_part, c->red_part, c->result,
+    void* bufs[] = {c->f[0], c->f[1], c->phi, c->phi_alt, c->phi2[0], c->phi2[1], c->step_part, c->red_part, c->result,
                     c->scratch, c->dev_err,
                     c->vel.sx2, c->vel.s2x, c->vel.sy2, c->vel.s2y,
                     c->vel.pu[0], c->vel.pu[1], c->vel.pv[0], c->vel.pv[1]};
@@ -574,6 +630,7 @@ static int init_impl(lbm_ace_ctx* c, const lbm_ace_params* p)
     } else {
         CK(c, cudaMalloc(&c->phi, n * c->elem));
     }
+    if (p->kernel_variant == 6) CK(c, cudaMalloc(&c->phi_alt, n * sizeof(float)));
     CK(c, cudaMalloc(&c->result, 2 * sizeof(double)));
 
     CK(c, cudaMalloc(&c->dev_err, sizeof(int)));
@@ -715,8 +772,12 @@ int lbm_ace_init(const lbm_ace_params* p, lbm_ace_ctx** out)
         return fail(nullptr, LBM_ACE_EINVAL, "disk centre/radius not finite");
     }
     if (p->rows_per_cta < 0) return fail(nullptr, LBM_ACE_EINVAL, "rows_per_cta must be >= 0");
-    if (p->kernel_variant < 0 || p->kernel_variant > 4)
+    if (p->kernel_variant < 0 || p->kernel_variant > 6 || p->kernel_variant == 5)
         return fail(nullptr, LBM_ACE_EINVAL, "kernel_variant %d unknown", p->kernel_variant);
+    if (p->kernel_variant == 6 && (p->precision != LBM_ACE_F32 || p->nx % 2 != 0 ||
+                                   p->velocity_kind == LBM_ACE_VEL_CALLBACK))
+        return fail(nullptr, LBM_ACE_EINVAL,
+                    "kernel_variant 6 needs FP32, an even nx and a vortex, uniform or field velocity");
     if (p->kernel_variant == 4 && p->nx % 2 != 0)
         return fail(nullptr, LBM_ACE_EINVAL, "kernel_variant 4 needs an even nx (nx = %d)", p->nx);
     if (p->kernel_variant == 2) {
@@ -750,6 +811,17 @@ int lbm_ace_step(lbm_ace_ctx* c, long long n)
     if (n < 0) return fail(c, LBM_ACE_EINVAL, "n = %lld: must be >= 0", n);
     DeviceGuard g(c->dev);
     for (long long s = 0; s < n; ++s) {
+        if (c->variant == 6 && n - s >= 2) { // two steps in one launch
+            launch_tb2_any(c);
+            CK(c, cudaGetLastError());
+            c->cur = 1 - c->cur;
+            std::swap(c->phi, c->phi_alt);
+            c->t += 2;
+            c->stepped = true;
+            c->fresh = false;
+            ++s;
+            continue;
+        }
         if (c->p.velocity_kind == LBM_ACE_VEL_CALLBACK && c->t > 0) {
             // u(t) into the pair that held u(t-2); the pair with u(t-1) becomes "previous"
             const int next = 1 - c->vel.cur;

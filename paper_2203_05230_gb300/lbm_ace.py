@@ -28,6 +28,7 @@ MODEL_MODIFIED, MODEL_CONSERVATIVE = 0, 1
 VEL_SINGLE_VORTEX, VEL_UNIFORM, VEL_FIELD, VEL_CALLBACK = 0, 1, 2, 3
 # fused step kernel variant
 KERNEL_AUTO, KERNEL_DIRECT, KERNEL_BULK, KERNEL_WARP, KERNEL_PAIR = 0, 1, 2, 3, 4
+KERNEL_DEV, KERNEL_TWO_STEP = 5, 6
 
 VELOCITY_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
