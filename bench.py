@@ -86,6 +86,24 @@ def dist_setup():
     return ws, rank, local
 
 
+def max_over_ranks(secs: float, ws: int, device=None) -> float:
+    """The job's time is the slowest replica's: MAX over the ranks of the process group
+    (a no-op for one rank)."""
+    if ws <= 1:
+        return secs
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([secs], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mlups(ws: int, lups_per_rank: int, secs: float) -> float:
+    """Whole-job throughput: every rank advances its own replica by lups_per_rank node
+    updates in the (max-over-ranks) time secs."""
+    return ws * lups_per_rank / secs / 1e6
+
+
 class ClockSampler:
     """nvidia-smi samples during the timed region (SM clock, throttle reasons)."""
     Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
@@ -284,12 +302,9 @@ def run_ours(args):
         note = f"first measurement rejected for clocks {clk}; re-measured"
         clk = cs.summary()
     m1 = lat.mass()
-    if ws > 1:
-        t = torch.tensor([secs], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        secs = float(t.item())
+    secs = max_over_ranks(secs, ws, "cuda")
     lups = args.L * args.L * args.steps
-    value = ws * lups / secs / 1e6
+    value = job_mlups(ws, lups, secs)
     spl = STEPS_PER_LAUNCH.get(shape[4], 1)
     launches = args.steps // spl + args.steps % spl
     per_launch = secs / launches
