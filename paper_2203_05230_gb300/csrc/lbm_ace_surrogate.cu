@@ -823,8 +823,13 @@ __global__ void __launch_bounds__(256) surr_out_bwd(const bf16* __restrict__ a4,
     const int tid = threadIdx.x;
     for (int k = tid; k < L5_N; k += blockDim.x)
         w[k] = k < 288 ? __bfloat162float(__float2bfloat16_rn(params[OFF_W5 + k])) : params[OFF_W5 + k];
-    float acc0 = 0.0f, acc1 = 0.0f;
-    const int k0 = tid, k1 = tid + 256; // outputs of this thread (k1 valid when < 289)
+    // weight gradient: thread (ci, row group rg) owns dW_5[ci][0..8] over tile rows 2 rg, 2 rg + 1,
+    // sliding a 3 x 3 window of a_4 channel ci along each row (3 shared loads per pixel)
+    const int wci = tid & 31, rg = tid >> 5;
+    float acc[9];
+#pragma unroll
+    for (int t = 0; t < 9; ++t) acc[t] = 0.0f;
+    float bacc = 0.0f;
     for (long long tile = blockIdx.x; tile < g.ntiles; tile += gridDim.x) {
         int b, y0, x0;
         tile_origin(g, tile, b, y0, x0);
@@ -838,22 +843,30 @@ __global__ void __launch_bounds__(256) surr_out_bwd(const bf16* __restrict__ a4,
         cp_wait<0>();
         __syncthreads();
         const int vr = min(TH, g.H - y0), vc = min(TW, g.W - x0); // valid rows / columns of the tile
-        // weight gradient partials
+#pragma unroll 1
+        for (int r = 2 * rg; r < 2 * rg + 2 && r < vr; ++r) {
+            float wv[3][3];
 #pragma unroll
-        for (int s = 0; s < 2; ++s) {
-            const int k = s ? k1 : k0;
-            if (k >= L5_N) continue;
-            float a = 0.0f;
-            if (k == 288) {
-                for (int r = 0; r < vr; ++r)
-                    for (int c = 0; c < vc; ++c) a += gh[(r + 1) * HWD + c + 1];
-            } else {
-                const int ci = k / 9, tap = k - 9 * (k / 9), j = tap / 3, i = tap % 3;
-                for (int r = 0; r < vr; ++r)
-                    for (int c = 0; c < vc; ++c)
-                        a = fmaf(gh[(r + 1) * HWD + c + 1], __bfloat162float(hs[((r + j) * HWD + c + i) * PS + ci]), a);
+            for (int j = 0; j < 3; ++j)
+#pragma unroll
+                for (int i = 0; i < 3; ++i) wv[j][i] = __bfloat162float(hs[((r + j) * HWD + i) * PS + wci]);
+#pragma unroll 1
+            for (int c = 0; c < vc; ++c) {
+                const float gq = gh[(r + 1) * HWD + c + 1];
+                bacc += gq;
+#pragma unroll
+                for (int j = 0; j < 3; ++j)
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) acc[j * 3 + i] = fmaf(gq, wv[j][i], acc[j * 3 + i]);
+                if (c + 1 < vc) {
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) {
+                        wv[j][0] = wv[j][1];
+                        wv[j][1] = wv[j][2];
+                        wv[j][2] = __bfloat162float(hs[((r + j) * HWD + c + 3) * PS + wci]);
+                    }
+                }
             }
-            if (s) acc1 += a; else acc0 += a;
         }
         // dL/dz_4 at the tile's own pixels
         {
@@ -889,24 +902,42 @@ __global__ void __launch_bounds__(256) surr_out_bwd(const bf16* __restrict__ a4,
         }
         __syncthreads();
     }
+    // the eight row groups' sums, added in order of rg (the halo buffer is free now)
+    float* red = reinterpret_cast<float*>(smem);              // [8][L5_N]
+#pragma unroll
+    for (int t = 0; t < 9; ++t) red[rg * L5_N + wci * 9 + t] = acc[t];
+    if (wci == 0) red[rg * L5_N + 288] = bacc;
+    __syncthreads();
     float* out = part + (size_t)blockIdx.x * L5_N;
-    out[k0] = acc0;
-    if (k1 < L5_N) out[k1] = acc1;
+    for (int k = tid; k < L5_N; k += 256) {
+        float sum = 0.0f;
+        for (int q = 0; q < 8; ++q) sum += red[q * L5_N + k];
+        out[k] = sum;
+    }
 }
 
 // Layer 1 weight gradient per tile: part[cta][co * 27 + ci * 9 + tap] and part[cta][864 + co].
-__global__ void __launch_bounds__(256) surr_in_wgrad(const bf16* __restrict__ gz1, const float* __restrict__ phi,
-                                                     const float* __restrict__ u, const float* __restrict__ v,
-                                                     float* __restrict__ part, const Geo g)
+// Thread (co, ci, rg) owns dW_1[co][ci][0..8] over tile rows 4 rg .. 4 rg + 3, sliding a
+// 3 x 3 window of input channel ci along each row (one gz load and 3 input loads per
+// pixel); the row groups are added in order at the end.
+constexpr int IW_THREADS = 384;
+
+__global__ void __launch_bounds__(IW_THREADS) surr_in_wgrad(const bf16* __restrict__ gz1, const float* __restrict__ phi,
+                                                            const float* __restrict__ u, const float* __restrict__ v,
+                                                            float* __restrict__ part, const Geo g)
 {
-    __shared__ float gsm[TH * TW][C + 1];
+    __shared__ float gsm[TH * TW][C + 1];   // also the final reduction buffer [4][L1_N]
     __shared__ float xs[3][HPX];
     const int tid = threadIdx.x;
-    float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    const int co = tid & 31, ci = (tid >> 5) % 3, rg = tid / 96;
+    float acc[9];
+#pragma unroll
+    for (int t = 0; t < 9; ++t) acc[t] = 0.0f;
+    float bacc = 0.0f;
     for (long long tile = blockIdx.x; tile < g.ntiles; tile += gridDim.x) {
         int b, y0, x0;
         tile_origin(g, tile, b, y0, x0);
-        {
+        if (tid < TH * TW) {
             const int r = tid / TW, c = tid % TW;
             const int y = y0 + r, x = x0 + c;
             if (y < g.H && x < g.W) {
@@ -924,10 +955,10 @@ __global__ void __launch_bounds__(256) surr_in_wgrad(const bf16* __restrict__ gz
                 }
             } else {
 #pragma unroll
-                for (int k = 0; k < C; ++k) gsm[tid][k] = 0.0f;
+                for (int k = 0; k < C; ++k) gsm[tid][k] = 0.0f; // pixels outside the image add nothing
             }
         }
-        for (int q = tid; q < HPX; q += 256) {
+        for (int q = tid; q < HPX; q += IW_THREADS) {
             const int hy = q / HWD, hx = q - hy * HWD;
             const int y = wrap_halo(y0 + hy - 1, g.H), x = wrap_halo(x0 + hx - 1, g.W);
             const size_t k = ((size_t)b * g.H + y) * g.W + x;
@@ -936,28 +967,42 @@ __global__ void __launch_bounds__(256) surr_in_wgrad(const bf16* __restrict__ gz
             xs[2][q] = v[k] * U_SCALE;
         }
         __syncthreads();
+#pragma unroll 1
+        for (int r = 4 * rg; r < 4 * rg + 4; ++r) {
+            float wv[3][3];
 #pragma unroll
-        for (int s = 0; s < 4; ++s) {
-            const int k = tid + 256 * s;
-            if (k >= L1_N) continue;
-            float a = 0.0f;
-            if (k >= 864) {
-                const int co = k - 864;
-                for (int q = 0; q < TH * TW; ++q) a += gsm[q][co];
-            } else {
-                const int co = k / 27, ci = (k / 9) % 3, tap = k % 9, j = tap / 3, i = tap % 3;
-                for (int r = 0; r < TH; ++r)
-                    for (int c = 0; c < TW; ++c) a = fmaf(gsm[r * TW + c][co], xs[ci][(r + j) * HWD + c + i], a);
+            for (int j = 0; j < 3; ++j)
+#pragma unroll
+                for (int i = 0; i < 3; ++i) wv[j][i] = xs[ci][(r + j) * HWD + i];
+#pragma unroll 4
+            for (int c = 0; c < TW; ++c) {
+                const float gq = gsm[r * TW + c][co];
+                bacc += gq;
+#pragma unroll
+                for (int j = 0; j < 3; ++j)
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) acc[j * 3 + i] = fmaf(gq, wv[j][i], acc[j * 3 + i]);
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    wv[j][0] = wv[j][1];
+                    wv[j][1] = wv[j][2];
+                    wv[j][2] = xs[ci][(r + j) * HWD + min(c + 3, HWD - 1)];
+                }
             }
-            acc[s] += a;
         }
         __syncthreads();
     }
-    float* out = part + (size_t)blockIdx.x * L1_N;
+    float* red = &gsm[0][0];                 // [4][L1_N]
 #pragma unroll
-    for (int s = 0; s < 4; ++s) {
-        const int k = tid + 256 * s;
-        if (k < L1_N) out[k] = acc[s];
+    for (int t = 0; t < 9; ++t) red[rg * L1_N + co * 27 + ci * 9 + t] = acc[t];
+    if (ci == 0) red[rg * L1_N + 864 + co] = bacc;
+    __syncthreads();
+    float* out = part + (size_t)blockIdx.x * L1_N;
+    for (int k = tid; k < L1_N; k += IW_THREADS) {
+        float sum = 0.0f;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) sum += red[q * L1_N + k];
+        out[k] = sum;
     }
 }
 
@@ -1295,7 +1340,7 @@ int lbm_ace_net_create(int device, void* stream, lbm_ace_net** out)
     n->wg_grid = std::max(1, occ) * n->sms;
     CREATE_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, surr_out_bwd, 256, n->ob_smem));
     n->ob_grid = std::max(1, occ) * n->sms;
-    CREATE_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, surr_in_wgrad, 256, 0));
+    CREATE_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, surr_in_wgrad, IW_THREADS, 0));
     n->iw_grid = std::max(1, occ) * n->sms;
     n->wpart_n = (size_t)std::max({(size_t)n->wg_grid * LH_N, (size_t)n->ob_grid * L5_N, (size_t)n->iw_grid * L1_N});
     CREATE_CK(cudaMalloc(&n->wpart, n->wpart_n * sizeof(float)));
@@ -1386,7 +1431,7 @@ int lbm_ace_net_loss_grad(lbm_ace_net* n, const float* phi, const float* u, cons
     }
     // layer 1
     const int giw = (int)std::min<long long>(g.ntiles, n->iw_grid);
-    surr_in_wgrad<<<giw, 256, 0, n->stream>>>(n->gzb[cur], phi, u, v, n->wpart, g);
+    surr_in_wgrad<<<giw, IW_THREADS, 0, n->stream>>>(n->gzb[cur], phi, u, v, n->wpart, g);
     surr_reduce<<<(L1_N + 31) / 32, 256, 0, n->stream>>>(n->wpart, giw, L1_N, L1_N, n->grad + OFF_W1);
     NCK(n, cudaGetLastError());
     n->have_grad = true;
