@@ -63,7 +63,7 @@ def parse():
     ap.add_argument("--surr-batch", type=int, default=16, help="images per timed forward (surrogate mode)")
     ap.add_argument("--surr-traj", type=int, default=625,
                     help="training trajectories of 32 windows (surrogate mode; 0: forward timing only)")
-    ap.add_argument("--surr-train-steps", type=int, default=6000)
+    ap.add_argument("--surr-train-steps", type=int, default=20000)
     return ap.parse_args()
 
 

@@ -118,8 +118,9 @@ void lbm_ace_net_destroy(lbm_ace_net* net);
  * window was a surrogate window). The lattice may have any storage precision and a
  * vortex, uniform or field velocity; it must work on the same stream as the net.
  * Up to 8 surrogate windows run back to back on the device before the host reads
- * their checks (one synchronisation per group); the windows after a rejected one are
- * discarded, so the result is the same as checking window by window.
+ * their checks (one synchronisation per group; the group shrinks to one window after a
+ * rejection and doubles after each group without one); the windows after a rejected
+ * one are discarded, so the result is the same as checking window by window.
  * stats (may be NULL) receives the counts and the extreme deviations accepted. */
 typedef struct {
     long long windows;           /* windows advanced */

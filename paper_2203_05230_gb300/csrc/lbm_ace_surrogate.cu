@@ -35,6 +35,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <utility>
 #include <vector>
 
 namespace surr {
@@ -171,6 +172,13 @@ __device__ __forceinline__ float2 gelu_grad2(float2 z)
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 
+// Programmatic dependent launch: let the next kernel of the forward chain be scheduled
+// early, then wait until the previous one has finished and its writes are visible.
+// Both are no-ops for an ordinary launch.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_enter() { pdl_trigger(); pdl_wait(); }
+
 __device__ __forceinline__ void cp_async16(void* dst, const void* src)
 {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(dst)), "l"(src));
@@ -256,6 +264,7 @@ __global__ void __launch_bounds__(256) surr_in_fwd(const float* __restrict__ phi
 {
     __shared__ __align__(16) float wt[27][C];
     __shared__ __align__(16) float bs[C];
+    pdl_enter();
     for (int k = threadIdx.x; k < 864; k += blockDim.x) wt[k % 27][k / 27] = params[OFF_W1 + k];
     if (threadIdx.x < C) bs[threadIdx.x] = params[OFF_W1 + 864 + threadIdx.x];
     __syncthreads();
@@ -456,6 +465,8 @@ __global__ void __launch_bounds__(UMMA_THREADS, 1) surr_conv_umma(const bf16* __
     const unsigned b_full = smem_u32(&bars[0]), b_empty = smem_u32(&bars[2]);
     const unsigned b_tfull = smem_u32(&bars[4]), b_tempty = smem_u32(&bars[6]);
 
+    pdl_trigger();
+    // the prologue (weights, barriers, tensor memory) touches nothing the previous kernel writes
     for (int k = tid; k < WBYTES / 16; k += UMMA_THREADS) cp_async16(ws + k * 16, wu + k * 8);
     cp_commit();
     if (tid < 32) bv[tid] = (MODE == MODE_FWD || (MODE == MODE_OUT && tid == 0)) ? bias[tid] : 0.0f;
@@ -480,6 +491,7 @@ __global__ void __launch_bounds__(UMMA_THREADS, 1) surr_conv_umma(const bf16* __
     const unsigned tmem = tslot;
     const int per = g.tx * g.ty;
     bool failed = false;
+    pdl_wait();
 
     if (warp < U_LOAD_WARPS) {
         // ---- loaders: thread lt copies channel chunk kc = lt % 4 of halo columns
@@ -757,6 +769,7 @@ __global__ void __launch_bounds__(256) surr_residual(const float* __restrict__ p
                                                      float* __restrict__ out, int H, int W)
 {
     __shared__ double red[256];
+    pdl_enter();
     const int b = blockIdx.y;
     const long long HWn = (long long)H * W;
     const double m = block_sum_ordered(tsum + (size_t)b * tpi, tpi, red) / (double)HWn;
@@ -1237,24 +1250,45 @@ int check_dims(lbm_ace_net* n, int B, int H, int W)
 }
 
 // Forward pass into n->z / n->a (z stored when keep_z) and out.
+template <typename... KArgs, typename... Args>
+void launch_chain(void (*kernel)(KArgs...), dim3 grid, int threads, size_t smem, cudaStream_t stream, Args&&... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
 int run_forward(lbm_ace_net* n, const float* phi, const float* u, const float* v, float* out, int B, int H, int W,
                 bool keep_z)
 {
+    // the forward chain is launched with programmatic stream serialisation (each kernel
+    // waits for its predecessor with griddepcontrol.wait before reading its output)
     const UGeo g = make_ugeo(B, H, W);
     const long long P = (long long)B * H * W;
-    surr_in_fwd<<<grid1((P + 1) / 2, n->sms), 256, 0, n->stream>>>(phi, u, v, n->params, keep_z ? n->z[0] : nullptr, n->a[0],
-                                                         B, H, W);
+    launch_chain(surr_in_fwd, dim3(grid1((P + 1) / 2, n->sms)), 256, 0, n->stream, phi, u, v,
+                 (const float*)n->params, keep_z ? n->z[0] : nullptr, n->a[0], B, H, W);
     const int grid = (int)std::min<long long>(g.ntiles, n->conv_grid);
     for (int l = 0; l < 3; ++l) {
-        surr_conv_umma<MODE_FWD, 32><<<grid, UMMA_THREADS, n->conv_smem, n->stream>>>(
-            n->a[l], n->wu + (size_t)l * 9 * C * C, n->params + OFF_W2 + l * LH_N + 9216, nullptr,
-            keep_z ? n->z[l + 1] : nullptr, n->a[l + 1], nullptr, nullptr, g, n->derr);
+        launch_chain(surr_conv_umma<MODE_FWD, 32>, dim3(grid), UMMA_THREADS, n->conv_smem, n->stream,
+                     (const bf16*)n->a[l], (const bf16*)(n->wu + (size_t)l * 9 * C * C),
+                     (const float*)(n->params + OFF_W2 + l * LH_N + 9216), (const bf16*)nullptr,
+                     keep_z ? n->z[l + 1] : (bf16*)nullptr, n->a[l + 1], (float*)nullptr, (double*)nullptr, g,
+                     n->derr);
     }
     const int gout = (int)std::min<long long>(g.ntiles, n->out_grid);
-    surr_conv_umma<MODE_OUT, 16><<<gout, UMMA_THREADS, n->out_smem, n->stream>>>(
-        n->a[3], n->w5u, n->params + OFF_W5 + 288, nullptr, nullptr, nullptr, n->z5, n->tsum, g, n->derr);
-    surr_residual<<<dim3(red_blocks(H, W), B), 256, 0, n->stream>>>(phi, n->z5, n->tsum, (int)(g.tx * g.ty * U_TSUM),
-                                                                     out, H, W);
+    launch_chain(surr_conv_umma<MODE_OUT, 16>, dim3(gout), UMMA_THREADS, n->out_smem, n->stream,
+                 (const bf16*)n->a[3], (const bf16*)n->w5u, (const float*)(n->params + OFF_W5 + 288),
+                 (const bf16*)nullptr, (bf16*)nullptr, (bf16*)nullptr, n->z5, n->tsum, g, n->derr);
+    launch_chain(surr_residual, dim3(red_blocks(H, W), B), 256, 0, n->stream, phi, (const float*)n->z5,
+                 (const double*)n->tsum, (int)(g.tx * g.ty * U_TSUM), out, H, W);
     NCK(n, cudaGetLastError());
     return LBM_ACE_OK;
 }
@@ -1590,10 +1624,11 @@ int lbm_ace_hybrid_advance(lbm_ace_ctx* lat, lbm_ace_net* n, long long windows, 
     const int K = LBM_ACE_NET_K;
     std::vector<double> hp((size_t)HYB_DEPTH * 3 * rb);
     long long w = 0;
+    int run_ahead = HYB_DEPTH; // speculation depth: 1 after a rejection, doubled after each clean group
     while (w < windows) {
-        // up to HYB_DEPTH surrogate windows back to back, each field in the next ring slot,
-        // with its checks reduced on the device; one synchronisation for the batch
-        const int depth = (int)std::min<long long>(HYB_DEPTH, windows - w);
+        // up to run_ahead surrogate windows back to back, each field in the next ring slot,
+        // with its checks reduced on the device; one synchronisation for the group
+        const int depth = (int)std::min<long long>(run_ahead, windows - w);
         for (int j = 0; j < depth; ++j) {
             LAT(lbm_ace_velocity_device(lat, (double)(t + (long long)j * K) + 0.5 * K, u, v));
             rc = run_forward(n, ring[(c + j) % NB], u, v, ring[(c + j + 1) % NB], 1, ny, nx, false);
@@ -1625,6 +1660,7 @@ int lbm_ace_hybrid_advance(lbm_ace_ctx* lat, lbm_ace_net* n, long long windows, 
             st.windows += acc;
             w += acc;
         }
+        run_ahead = acc < depth ? 1 : std::min(HYB_DEPTH, 2 * run_ahead);
         if (acc < depth) { // the first rejected window: K lattice Boltzmann steps from ring[c]
             if (stale) LAT(lbm_ace_reset_device(lat, ring[c], t));
             LAT(lbm_ace_step(lat, K));

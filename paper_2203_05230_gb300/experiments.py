@@ -20,7 +20,11 @@ the results (phi-L1/L2 against a reference field, mass drift, interface width).
   held-out trajectories against persistence, then rolled out over one period of the
   256^2 vortex with the lattice Boltzmann fallback, against the plain FP32 run.
 
-Run: python -m paper_2203_05230_gb300.experiments {ablation,fp32,precision,batch,surrogate} (one GPU).
+* ``surrogate_sweep``: the rollout's error and speed against the fallback's width
+  tolerance, for two training lengths.
+
+Run: python -m paper_2203_05230_gb300.experiments
+{ablation,fp32,precision,batch,surrogate,surrogate_sweep} (one GPU).
 The paper's eps is 4x the eps used here (psi = eps ln(phi / (1 - phi)) as printed
 in Eq. 13); tables give both.
 """
@@ -161,7 +165,7 @@ def batch_study(count=256, steps=20, tune_steps=3):
             "speedup": dt_s / dt_g}
 
 
-def surrogate_study(n_traj=625, pairs=32, steps=6000, batch=16, held_out=25, L=256, seed=0, lr_max=2e-3,
+def surrogate_study(n_traj=625, pairs=32, steps=20000, batch=16, held_out=25, L=256, seed=0, lr_max=2e-3,
                     save_params=None):
     """Train the surrogate on trajectories 0 .. n_traj - held_out - 1 and report held-out
     errors, the untrained network's error, training throughput and the vortex rollout;
@@ -196,13 +200,43 @@ def surrogate_study(n_traj=625, pairs=32, steps=6000, batch=16, held_out=25, L=2
     return out
 
 
+def surrogate_sweep(n_traj=625, pairs=32, steps_list=(6000, 20000), batch=16, held_out=25, L=256, seed=0,
+                    width_tols=(0.1, 0.05, 0.03, 0.02, 0.01)):
+    """Accuracy against speed of the hybrid rollout: for each training length, the
+    held-out error and one 256^2 vortex period at several interface-width tolerances of
+    the fallback check (tighter tolerances send more windows to the LB solver)."""
+    import torch
+    from . import surrogate as SG
+    s = torch.cuda.current_stream()
+    data = SG.generate(n_traj, pairs, L=L, seed=seed, stream=s)
+    n_train = (n_traj - held_out) * pairs
+    train_idx, test_idx = np.arange(n_train), np.arange(n_train, data.n_pairs)
+    out = {"study": f"hybrid rollout of the {L}^2 vortex period against the fallback's width tolerance",
+           "runs": []}
+    for steps in steps_list:
+        with A.Net(0, s) as net:
+            net.set_params(W.surrogate_init_params(seed=seed))
+            tr = SG.Trainer(net, data, batch=batch, seed=seed)
+            t0 = time.perf_counter()
+            tr.train(steps, train_pairs=train_idx)
+            run = {"adam_steps": steps, "train_seconds": time.perf_counter() - t0, "held_out": tr.evaluate(test_idx),
+                   "rollouts": []}
+            for wt in width_tols:
+                ro = SG.vortex_rollout(net, L=L, width_tol=wt, stream=s)
+                run["rollouts"].append({"width_tol": wt, **{k: ro[k] for k in (
+                    "E2_vs_lbm_T", "E2_vs_lbm_half", "speedup", "surrogate_windows", "fallback_windows",
+                    "max_width_dev", "mass_drift_hybrid")}})
+            out["runs"].append(run)
+    return out
+
+
 def main(argv):
     which = argv[1] if len(argv) > 1 else "ablation"
     if which == "surrogate":
         res = surrogate_study(save_params=argv[2] if len(argv) > 2 else None)
     else:
         res = {"ablation": paper_ablation, "fp32": fp32_study, "precision": precision_study,
-               "batch": batch_study}[which]()
+               "batch": batch_study, "surrogate_sweep": surrogate_sweep}[which]()
     print(json.dumps(res))
 
 
