@@ -222,6 +222,9 @@ __global__ void __launch_bounds__(PAIR_THREADS, 5) ace_step_dev(const DevArgs<S>
         rec(7, C::hi(nxt.v[7]), C::one((unsigned short)r7), P2.c[2], P2.c[3]);
         rec(8, C::one((unsigned short)l8), C::lo(nxt.v[8]), P2.c[0], P2.c[1]);
         const float hfk = hg + hs_w * hp;
+        // the raw sets are consumed: load the next row now, so it overlaps this whole iteration
+        const typename Vel::Row vr = vr_next;
+        if (k + 1 < nk) fetch(k + 1);
         float2 s2 = make_float2(0.0f, 0.0f);
 #pragma unroll
         for (int i = 0; i < 9; ++i) s2 = __fadd2_rn(s2, make_float2(fa[i], fb[i]));
@@ -241,9 +244,7 @@ __global__ void __launch_bounds__(PAIR_THREADS, 5) ace_step_dev(const DevArgs<S>
             if (lane == 16) chi_s[k & 3][w + 2] = chi_of<float, MODEL>(hs, a);
         }
         __syncthreads();
-        const typename Vel::Row vr = vr_next;
         const float ppa = P0.c[1], ppb = P0.c[2]; // phi(t-1) of the colliding row r - 1
-        if (k + 1 < nk) fetch(k + 1);
         if (k >= 2) {
             const int yc = y0 + k - 2;
             const int j = act ? 2 * tx : w - 2;

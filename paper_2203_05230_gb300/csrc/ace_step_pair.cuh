@@ -144,6 +144,10 @@ __device__ __forceinline__ void pair_tile(const StepArgs<T>& a, const Vel& vel, 
         T fa[9], fb[9];
         unpack(nxt, fa, fb);
         const T hvk = hv;
+        // what the row colliding below needs from the raw set, before it is refilled
+        const T ppa = pp_a, ppb = pp_b;
+        const typename Vel::Row vr = vr_next;
+        if (k + 1 < nk) fetch(k + 1); // the loads of row k + 1 overlap this whole iteration
         T sa, sb; // phi of both nodes, summed in order 0..8 like every other variant
         if constexpr (sizeof(T) == 4) {
             float2 s2 = make_float2(0.0f, 0.0f);
@@ -172,9 +176,6 @@ __device__ __forceinline__ void pair_tile(const StepArgs<T>& a, const Vel& vel, 
             if (lane == 16) chi_s[k & 3][w + 2] = chi_of<T, MODEL>(hs, a);
         }
         __syncthreads();
-        const T ppa = pp_a, ppb = pp_b;
-        const typename Vel::Row vr = vr_next;
-        if (k + 1 < nk) fetch(k + 1);
         if (k >= 2) {
             const int yc = y0 + k - 2;
             const int j = act ? 2 * tx : w - 2; // ring column of xa - 1 is j + 1
