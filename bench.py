@@ -55,7 +55,8 @@ def parse():
     ap.add_argument("--L", type=int, default=2048)
     ap.add_argument("--precision", default="f32", choices=["f32", "f64", "f16dev", "bf16dev"])
     ap.add_argument("--rows", type=int, default=0, help="rows per CTA (0: library default)")
-    ap.add_argument("--variant", type=int, default=0, help="step kernel: 0 auto, 1 direct loads, 2 bulk-copy pipeline, 3 independent warps, 4 column pairs")
+    ap.add_argument("--variant", type=int, default=0, help="step kernel: 0 auto, 1 direct loads, 2 bulk-copy pipeline, 3 independent warps, 4 column pairs, "
+                    "6 two steps per launch")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)

@@ -75,6 +75,7 @@ struct StepArgs {
     long long plane;           // nx * ny
     int rows;                  // rows per CTA
     int first;                 // t == 0: no time-derivative term
+    int tdir;                  // t & 1: march direction of the row bands (column-pair kernels)
     T omega;                   // 1 / tau
     T fpref;                   // 1 - 1 / (2 tau)
     T eps, inv_eps, inv4eps;   // eps, 1/eps, 1/(4 eps)

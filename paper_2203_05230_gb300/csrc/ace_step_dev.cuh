@@ -67,16 +67,12 @@ struct DevArgs {
     float* __restrict__ phout;              // phi(t)
 };
 
-template <typename S, int MODEL, class Vel>
-__global__ void __launch_bounds__(PAIR_THREADS, 5) ace_step_dev(const DevArgs<S> d, const StepArgs<float> a, const Vel vel)
+// The tile (blockIdx.x, blockIdx.y) of one step. UP: march the rows upwards (march_up).
+template <typename S, int MODEL, class Vel, bool UP>
+__device__ __forceinline__ void dev_tile(const DevArgs<S>& d, const StepArgs<float>& a, const Vel& vel,
+                                         float (*chi_s)[PAIR_COLS + 4], double* red_s)
 {
     using C = Dev16<S>;
-    __shared__ __align__(16) float chi_s[4][PAIR_COLS + 4]; // index j holds column x0 + j - 2
-    __shared__ double red_s[PAIR_THREADS / 32];
-    // programmatic dependent launch (no-ops for an ordinary launch): see ace_step_pair
-    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
-    asm volatile("griddepcontrol.wait;\n" ::: "memory");
-
     const int tx = threadIdx.x;
     const int lane = tx & 31;
     const int x0 = blockIdx.x * PAIR_COLS;
@@ -136,8 +132,9 @@ __global__ void __launch_bounds__(PAIR_THREADS, 5) ace_step_dev(const DevArgs<S>
         if (own_right) r = q.r;
         p.c[0] = l; p.c[1] = q.v.x; p.c[2] = q.v.y; p.c[3] = r;
     };
-    auto fetch = [&](int k) { // pulled row r = y0 - 1 + k: deviations, and phi row r + 1
-        const int r = wrap_idx(y0 - 1 + k, a.ny);
+    // iteration k pulls row r(k) = y0 - 1 + k (UP: y1 - k) and collides row r(k - 1)
+    auto fetch = [&](int k) { // pulled row r(k): deviations, and phi row r(k + 1)
+        const int r = wrap_idx(UP ? y1 - k : y0 - 1 + k, a.ny);
         const int rm = r == 0 ? a.ny - 1 : r - 1, rp = r == a.ny - 1 ? 0 : r + 1;
         const unsigned o0 = (unsigned)r * nxu, om = (unsigned)rm * nxu, op = (unsigned)rp * nxu;
         const unsigned ua = (unsigned)xa;
@@ -162,24 +159,25 @@ __global__ void __launch_bounds__(PAIR_THREADS, 5) ace_step_dev(const DevArgs<S>
             nxt.r6 = d.gin[6u * plane + om + ur];
             nxt.r7 = d.gin[7u * plane + op + ur];
         }
-        load_phi(rp, pnx);
+        load_phi(UP ? rm : rp, pnx);
         if (halo) {
             const unsigned hsrc = (unsigned)wrap_idx(r - hcy, a.ny) * nxu + (unsigned)hcol;
             hg = C::one(d.gin[(unsigned)hi * plane + hsrc]);
             hp = d.phin[hsrc];
         }
-        const int yc = y0 + k - 2;
+        const int yc = UP ? y1 - k + 1 : y0 + k - 2;
         if (yc >= y0 && yc < y1) vr_next = vel.rowv(ca, xa, yc);
     };
 
-    // phi(t-1) rows r - 1, r, r + 1 around the pair of the pulled row r
-    PhiRow P0, P1, P2;
+    // phi(t-1) rows r(k - 1), r(k), r(k + 1) around the pair of the pulled row r(k), in
+    // march order: Qb behind, Qc at, Qa ahead (rows r - 1, r, r + 1 when marching down)
+    PhiRow Qb, Qc, Qa;
     {
         PhiRaw q;
-        load_phi(wrap_idx(y0 - 2, a.ny), q);
-        unpack_phi(q, P1);
-        load_phi(wrap_idx(y0 - 1, a.ny), q);
-        unpack_phi(q, P2);
+        load_phi(wrap_idx(UP ? y1 + 1 : y0 - 2, a.ny), q);
+        unpack_phi(q, Qc);
+        load_phi(wrap_idx(UP ? y1 : y0 - 1, a.ny), q);
+        unpack_phi(q, Qa);
     }
 
     float pa[9], pb[9];
@@ -191,9 +189,12 @@ __global__ void __launch_bounds__(PAIR_THREADS, 5) ace_step_dev(const DevArgs<S>
     fetch(0);
 #pragma unroll 1
     for (int k = 0; k < nk; ++k) {
-        P0 = P1;
-        P1 = P2;
-        unpack_phi(pnx, P2);
+        Qb = Qc;
+        Qc = Qa;
+        unpack_phi(pnx, Qa);
+        const PhiRow& P0 = UP ? Qa : Qb; // row r - 1
+        const PhiRow& P1 = Qc;           // row r
+        const PhiRow& P2 = UP ? Qb : Qa; // row r + 1
         // deviations of the pair, shifted planes completed from the neighbour lanes
         unsigned l1 = __shfl_up_sync(0xffffffffu, nxt.v[1], 1) >> 16;
         unsigned l5 = __shfl_up_sync(0xffffffffu, nxt.v[5], 1) >> 16;
@@ -244,13 +245,14 @@ __global__ void __launch_bounds__(PAIR_THREADS, 5) ace_step_dev(const DevArgs<S>
             if (lane == 16) chi_s[k & 3][w + 2] = chi_of<float, MODEL>(hs, a);
         }
         __syncthreads();
-        const float ppa = P0.c[1], ppb = P0.c[2]; // phi(t-1) of the colliding row r - 1
+        const float ppa = Qb.c[1], ppb = Qb.c[2]; // phi(t-1) of the colliding row r(k - 1)
         if (k >= 2) {
-            const int yc = y0 + k - 2;
+            const int yc = UP ? y1 - k + 1 : y0 + k - 2;
             const int j = act ? 2 * tx : w - 2;
-            const float* cS = chi_s[(k - 2) & 3] + 1 + j;
+            // ring slots of rows yc - 1 (S) and yc + 1 (N): the rows pulled at k - 2 and k
+            const float* cS = chi_s[(UP ? k : k - 2) & 3] + 1 + j;
             const float* cC = chi_s[(k - 1) & 3] + 1 + j;
-            const float* cN = chi_s[k & 3] + 1 + j;
+            const float* cN = chi_s[(UP ? k - 2 : k) & 3] + 1 + j;
             float2 o2[9];
             collide_pair<float, MODEL>(a, vel, ca, cb, vr, vel.rowv(cb, xb, yc), pa, pb, pha, phb, ppa, ppb, cS, cC, cN,
                                        o2);
@@ -283,6 +285,20 @@ __global__ void __launch_bounds__(PAIR_THREADS, 5) ace_step_dev(const DevArgs<S>
         for (int i = 0; i < PAIR_THREADS / 32; ++i) s += red_s[i];
         a.mass_part[(long long)blockIdx.y * gridDim.x + blockIdx.x] = s;
     }
+}
+
+template <typename S, int MODEL, class Vel>
+__global__ void __launch_bounds__(PAIR_THREADS, 5) ace_step_dev(const DevArgs<S> d, const StepArgs<float> a, const Vel vel)
+{
+    __shared__ __align__(16) float chi_s[4][PAIR_COLS + 4]; // index j holds column x0 + j - 2
+    __shared__ double red_s[PAIR_THREADS / 32];
+    // programmatic dependent launch (no-ops for an ordinary launch): see ace_step_pair
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
+    if (march_up(blockIdx.y, a.tdir))
+        dev_tile<S, MODEL, Vel, true>(d, a, vel, chi_s, red_s);
+    else
+        dev_tile<S, MODEL, Vel, false>(d, a, vel, chi_s, red_s);
 }
 
 // ---- state conversions for the deviation storage (init, read-out, checkpoints) ----

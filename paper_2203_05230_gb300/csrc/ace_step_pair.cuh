@@ -12,7 +12,9 @@
 // two halo columns of the strip are recomputed by lanes of warp 0 as in ace_step.
 // The per-node arithmetic is collide_node_row, shared with the other variants, and
 // phi is summed in the same order, so all variants agree bit for bit. Stores are
-// pairs too.
+// pairs too. Row bands alternate their march direction from band to band and from step
+// to step (march_up), so a band's halo rows and the previous step's last rows are read
+// from L2 rather than DRAM.
 //
 // Requirement (checked by the host): nx even, so every pair is aligned.
 #pragma once
@@ -24,12 +26,21 @@ namespace lbmace {
 constexpr int PAIR_THREADS = 128;
 constexpr int PAIR_COLS = 2 * PAIR_THREADS;
 
+// March direction of row band `by` in a step with parity tdir (t & 1): alternate bands
+// march in opposite directions and every band turns round at the next step. Two
+// neighbouring bands then reach their common edge together, so the rows both of them
+// read there (each band's halo) come from DRAM once and are found in L2 by the other;
+// and each step starts on the rows the previous step wrote last, still in L2.
+__device__ __forceinline__ bool march_up(unsigned by, int tdir) { return ((by + (unsigned)tdir) & 1u) != 0; }
+
 // One tile: columns [x0, x0 + 256) (clipped to nx) and rows [y0, y0 + a.rows) of the
 // lattice described by `a`. chi_s (4 x (PAIR_COLS + 4), 16-byte aligned: ring index j
 // holds column x0 + j - 2) and red_s (PAIR_THREADS / 32 doubles) are the CTA's shared
 // memory; thread 0 writes the tile's FP64 mass of phi(t) to *mass_out. Ends with a
 // barrier, so the CTA can take another tile right after.
-template <typename T, int MODEL, class Vel>
+// UP: march the rows from y1 - 1 up to y0 instead of down from y0; every node gets the
+// same arithmetic on the same values, only the order of the FP64 mass partial changes.
+template <typename T, int MODEL, class Vel, bool UP = false>
 __device__ __forceinline__ void pair_tile(const StepArgs<T>& a, const Vel& vel, int x0, int y0,
                                           T (*chi_s)[PAIR_COLS + 4], double* red_s, double* mass_out)
 {
@@ -72,8 +83,9 @@ __device__ __forceinline__ void pair_tile(const StepArgs<T>& a, const Vel& vel, 
     T pp_a = T(0), pp_b = T(0); // phi(t-1) of the row that collides next
     typename Vel::Row vr_next{};
 
-    auto fetch = [&](int k) { // pulled row r = y0 - 1 + k, plus what row y0 + k - 2 needs to collide
-        const int r = wrap_idx(y0 - 1 + k, a.ny);
+    // iteration k pulls row r(k) = y0 - 1 + k (UP: y1 - k) and collides row r(k - 1)
+    auto fetch = [&](int k) { // pulled row r(k), plus what row r(k - 1) needs to collide
+        const int r = wrap_idx(UP ? y1 - k : y0 - 1 + k, a.ny);
         const int rm = r == 0 ? a.ny - 1 : r - 1, rp = r == a.ny - 1 ? 0 : r + 1;
         const unsigned o0 = (unsigned)r * nxu, om = (unsigned)rm * nxu, op = (unsigned)rp * nxu;
         const unsigned ua = (unsigned)xa;
@@ -99,7 +111,7 @@ __device__ __forceinline__ void pair_tile(const StepArgs<T>& a, const Vel& vel, 
             nxt.r7 = a.fin[7u * plane + op + ur];
         }
         if (halo) hv = a.fin[hbase + (unsigned)wrap_idx(r - hcy, a.ny) * nxu];
-        const int yc = y0 + k - 2;
+        const int yc = UP ? y1 - k + 1 : y0 + k - 2;
         if (yc >= y0 && yc < y1) {
             if (!a.first) {
                 const V p2 = *reinterpret_cast<const V*>(a.phi + ((unsigned)yc * nxu + ua));
@@ -177,11 +189,13 @@ __device__ __forceinline__ void pair_tile(const StepArgs<T>& a, const Vel& vel, 
         }
         __syncthreads();
         if (k >= 2) {
-            const int yc = y0 + k - 2;
+            const int yc = UP ? y1 - k + 1 : y0 + k - 2;
             const int j = act ? 2 * tx : w - 2; // ring column of xa - 1 is j + 1
+            // ring slots of rows yc - 1 (S) and yc + 1 (N): the rows pulled at k - 2 and k
+            const int ks = UP ? k : k - 2, kn = UP ? k - 2 : k;
             V o2[9];
             collide_pair<T, MODEL>(a, vel, ca, cb, vr, vel.rowv(cb, xb, yc), pa, pb, pha, phb, ppa, ppb,
-                                   chi_s[(k - 2) & 3] + 1 + j, chi_s[(k - 1) & 3] + 1 + j, chi_s[k & 3] + 1 + j, o2);
+                                   chi_s[ks & 3] + 1 + j, chi_s[(k - 1) & 3] + 1 + j, chi_s[kn & 3] + 1 + j, o2);
             if (act) {
                 const unsigned o = (unsigned)yc * nxu + (unsigned)xa;
 #pragma unroll
@@ -222,8 +236,11 @@ __global__ void __launch_bounds__(PAIR_THREADS, sizeof(T) == 4 ? 5 : 1) ace_step
     // Both are no-ops for an ordinary launch.
     asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
     asm volatile("griddepcontrol.wait;\n" ::: "memory");
-    pair_tile<T, MODEL>(a, vel, blockIdx.x * PAIR_COLS, blockIdx.y * a.rows, chi_s, red_s,
-                        &a.mass_part[(long long)blockIdx.y * gridDim.x + blockIdx.x]);
+    double* mp = &a.mass_part[(long long)blockIdx.y * gridDim.x + blockIdx.x];
+    if (march_up(blockIdx.y, a.tdir))
+        pair_tile<T, MODEL, Vel, true>(a, vel, blockIdx.x * PAIR_COLS, blockIdx.y * a.rows, chi_s, red_s, mp);
+    else
+        pair_tile<T, MODEL, Vel, false>(a, vel, blockIdx.x * PAIR_COLS, blockIdx.y * a.rows, chi_s, red_s, mp);
 }
 
 } // namespace lbmace

@@ -113,6 +113,7 @@ StepArgs<T> make_args(lbm_ace_ctx* c)
     a.plane = (long long)c->p.nx * c->p.ny;
     a.rows = c->rows;
     a.first = c->fresh;
+    a.tdir = (int)(c->t & 1);
     a.omega = T(1.0 / c->p.tau);
     a.fpref = T(1.0 - 0.5 / c->p.tau);
     a.eps = T(c->p.eps);

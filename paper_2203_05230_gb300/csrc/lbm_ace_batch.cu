@@ -61,6 +61,7 @@ __device__ __forceinline__ void batch_tile(const BatchInst& I, float2 ph, int lt
     a.plane = (long long)I.nx * I.ny;
     a.rows = I.rows;
     a.first = t == 0;
+    a.tdir = t & 1; // unused by pair_tile's default downward march
     a.omega = I.omega; a.fpref = I.fpref;
     a.eps = I.eps; a.inv_eps = I.inv_eps; a.inv4eps = I.inv4eps;
     a.delta = I.delta; a.inv1p2d = I.inv1p2d;
@@ -478,6 +479,7 @@ int lbm_ace_batch_step_sequential(lbm_ace_batch* b, long long n)
             a.plane = (long long)I.nx * I.ny;
             a.rows = b->seq_rows[i];
             a.first = t == 0;
+            a.tdir = (int)(t & 1);
             a.omega = I.omega; a.fpref = I.fpref; a.eps = I.eps; a.inv_eps = I.inv_eps; a.inv4eps = I.inv4eps;
             a.delta = I.delta; a.inv1p2d = I.inv1p2d;
             VelVortex<float> v;

@@ -1,6 +1,7 @@
 """Two steps per launch (kernel variant 6, temporal blocking in shared memory): the
 same arithmetic on the same values as two launches of the column-pair kernel, so
-states, phi and the step mass must agree bit for bit with variant 4 for any step count
+states, phi and the state mass must agree bit for bit with variant 4 (the step mass up
+to its summation order) for any step count
 (odd counts end with one pair step), strip widths that do not fill the 256-column tile,
 lattices smaller than a tile, every velocity source and both models."""
 import numpy as np
@@ -28,7 +29,9 @@ def same(a, b):
     for (fa, pa, ma, ga, ta), (fb, pb, mb, gb, tb) in zip(a, b):
         assert ta == tb
         assert np.array_equal(fa, fb) and np.array_equal(pa, pb)
-        assert ma == mb and ga == gb
+        # the pair kernel alternates the bands' march direction, so its FP64 step-mass
+        # partials are summed in another order than the two-step kernel's
+        assert ga == gb and (ma == mb or abs(ma - mb) <= 1e-14 * abs(mb))
 
 
 VORTEX = dict(velocity_kind=A.VEL_SINGLE_VORTEX, U0=0.04, T_period=400.0, vortex_sign=-1.0)
