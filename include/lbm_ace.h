@@ -183,6 +183,18 @@ int lbm_ace_launch_shape(const lbm_ace_ctx* c, int* tile_x, int* rows_per_cta, i
 /* Block until all device work of the context has finished. */
 int lbm_ace_synchronize(lbm_ace_ctx* c);
 
+/* Failure-detection self-test (no GPU fault). Launches, on the context's stream, one
+ * CTA that initialises an mbarrier no thread ever arrives on and waits for it with the
+ * bounded wait the step kernels use (mbarrier.try_wait polled against clock64), giving
+ * up after `limit_cycles` SM clock cycles (1 .. 4e9; 2e6 is about 1 ms). The CTA then
+ * sets the context's device error flag, as a step kernel whose wait gave up does, and
+ * returns. The call synchronises the stream and reports through the same path as
+ * lbm_ace_synchronize: LBM_ACE_ETIMEOUT when the wait gave up (the expected result; the
+ * flag is cleared and the context stays usable), LBM_ACE_OK if the barrier somehow
+ * completed, LBM_ACE_EINVAL for a limit out of range, LBM_ACE_ECUDA on a CUDA error.
+ * The lattice state is not touched. */
+int lbm_ace_wait_selftest(lbm_ace_ctx* c, long long limit_cycles);
+
 /* ---- Device-side access (for a caller that keeps fields on the GPU) ---------------
  * These three calls are asynchronous on the context's stream and take DEVICE pointers
  * (on the context's device) to FP32 [ny][nx] arrays that the caller owns; each must

@@ -500,6 +500,19 @@ int check_device_error(lbm_ace_ctx* c)
     return LBM_ACE_OK;
 }
 
+// One CTA waits, with the step kernels' bounded wait, for an mbarrier nobody arrives on;
+// when the wait gives up it sets *err as a step kernel would (1), otherwise 0 is kept.
+__global__ void ace_wait_selftest(long long limit_cycles, int* err)
+{
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && !mbar_wait_bounded(&bar, 0, limit_cycles)) atomicExch(err, 1);
+}
+
 struct DeviceGuard {
     int prev = -1;
     explicit DeviceGuard(int d) { if (cudaGetDevice(&prev) == cudaSuccess && prev != d) cudaSetDevice(d); else prev = -1; }
@@ -1055,6 +1068,18 @@ int lbm_ace_launch_shape(const lbm_ace_ctx* c, int* tile_x, int* rows_per_cta, i
     if (grid_y) *grid_y = c->grid_y;
     if (kernel_variant) *kernel_variant = c->variant;
     return LBM_ACE_OK;
+}
+
+int lbm_ace_wait_selftest(lbm_ace_ctx* c, long long limit_cycles)
+{
+    if (!c) return fail(nullptr, LBM_ACE_EINVAL, "ctx is NULL");
+    if (limit_cycles < 1 || limit_cycles > kWaitLimitCycles)
+        return fail(c, LBM_ACE_EINVAL, "limit_cycles = %lld: must be in [1, %lld]", limit_cycles, kWaitLimitCycles);
+    DeviceGuard g(c->dev);
+    ace_wait_selftest<<<1, 32, 0, c->stream>>>(limit_cycles, c->dev_err);
+    CK(c, cudaGetLastError());
+    CK(c, cudaStreamSynchronize(c->stream));
+    return check_device_error(c);
 }
 
 int lbm_ace_synchronize(lbm_ace_ctx* c)

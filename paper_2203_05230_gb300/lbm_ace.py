@@ -44,7 +44,7 @@ EXPORTS = (
     "lbm_ace_batch_get_phi", "lbm_ace_batch_mass", "lbm_ace_batch_info", "lbm_ace_batch_steps_done",
     "lbm_ace_batch_synchronize", "lbm_ace_batch_last_error", "lbm_ace_batch_destroy",
     "lbm_ace_get_phi_device", "lbm_ace_velocity_device", "lbm_ace_reset_device", "lbm_ace_get_stream",
-    "lbm_ace_get_params",
+    "lbm_ace_get_params", "lbm_ace_wait_selftest",
     "lbm_ace_net_create", "lbm_ace_net_set_params", "lbm_ace_net_get_params", "lbm_ace_net_forward",
     "lbm_ace_net_loss_grad", "lbm_ace_net_adam", "lbm_ace_net_gather", "lbm_ace_net_metrics",
     "lbm_ace_net_synchronize", "lbm_ace_net_last_error", "lbm_ace_net_destroy", "lbm_ace_hybrid_advance",
@@ -117,6 +117,7 @@ def load(build_if_missing: bool = True):
     L.lbm_ace_steps_done.restype = ctypes.c_longlong
     L.lbm_ace_launch_shape.argtypes = [_P] + [ctypes.POINTER(ctypes.c_int)] * 5
     L.lbm_ace_synchronize.argtypes = [_P]
+    L.lbm_ace_wait_selftest.argtypes = [_P, ctypes.c_longlong]
     L.lbm_ace_last_error.argtypes = [_P]
     L.lbm_ace_last_error.restype = ctypes.c_char_p
     L.lbm_ace_status_string.argtypes = [ctypes.c_int]
@@ -314,6 +315,11 @@ class Lattice:
         _check(self.ctx, self._lib.lbm_ace_synchronize(self.ctx))
 
     synchronize = lbm_ace_synchronize
+
+    def lbm_ace_wait_selftest(self, limit_cycles: int) -> None:
+        """A device wait that nothing completes gives up after `limit_cycles` SM cycles;
+        raises LbmAceError with status ETIMEOUT, as a step whose wait gave up would."""
+        _check(self.ctx, self._lib.lbm_ace_wait_selftest(self.ctx, int(limit_cycles)))
 
     # -- device-side access (pointers are device addresses, e.g. tensor.data_ptr()) --
     def lbm_ace_get_phi_device(self, phi_ptr: int) -> None:
