@@ -203,21 +203,29 @@ def measured_peak():
 
 def cpu_baseline(args, v, seconds):
     """The FP64 oracle, as it stands, on all host cores: whole-lattice steps of the
-    same workload from t = 0 for about `seconds` of CPU work."""
+    same workload from t = 0 for about `seconds` of CPU work; then the same loop on one
+    thread for about a third of that (reported beside it, not as the baseline)."""
     import oracle as O
     th = O.threads_available()
     p = O.Params(nx=args.L, ny=args.L, tau=v.tau, eps=v.eps, U0=v.U0, T=v.T, sign=v.sign)
     s = O.Sim(p, v.phi0())
-    t0 = time.perf_counter()
-    s.step(1, threads=th)
-    one = time.perf_counter() - t0
-    n = max(1, min(2000, int(seconds / max(one, 1e-6))))
-    t0 = time.perf_counter()
-    s.step(n, threads=th)
-    dt = time.perf_counter() - t0
+
+    def timed(threads, budget):
+        t0 = time.perf_counter()
+        s.step(1, threads=threads)
+        one = time.perf_counter() - t0
+        n = max(1, min(2000, int(budget / max(one, 1e-6))))
+        t0 = time.perf_counter()
+        s.step(n, threads=threads)
+        return n, time.perf_counter() - t0
+
+    n, dt = timed(th, seconds)
+    n1, dt1 = timed(1, seconds / 3)
     return {"value": args.L * args.L * n / dt / 1e6, "unit": METRIC, "cores": th, "kind": "oracle",
             "sample": f"{n} whole-lattice FP64 oracle steps of the {args.L}x{args.L} vortex from t=1, "
-                      f"{th} OpenMP threads, {dt:.1f} s"}
+                      f"{th} OpenMP threads, {dt:.1f} s",
+            "single_thread": {"value": args.L * args.L * n1 / dt1 / 1e6, "unit": METRIC, "cores": 1,
+                              "sample": f"{n1} further steps of the same lattice on one thread, {dt1:.1f} s"}}
 
 
 def run_reference(args):
