@@ -68,6 +68,40 @@ def test_dev_full_period_256_phi_l2_and_mass(precision, bound, mbound):
     assert ms == pytest.approx(m1, rel=1e-5)
 
 
+@pytest.mark.parametrize("precision,tol", DEV)
+def test_dev_full_size_4096_sampled_nodes(precision, tol):
+    """The 4096^2 lattice of the 16-bit storage study, in the benchmark's launch shape: one
+    step from the stored (16-bit) form of an oracle-made state, checked at 512 sampled
+    nodes plus the corners and the tile seams against the oracle's per-node step of that
+    same stored state, and the mass bookkeeping of the step."""
+    L = 4096
+    v = W.vortex_fp32(L)
+    op = O.Params(nx=L, ny=L, tau=v.tau, eps=v.eps, U0=v.U0, T=float(v.T), sign=v.sign)
+    s = O.Sim(op, v.phi0()).step(2, threads=O.threads_available())
+    rng = np.random.default_rng(4096)
+    xs = np.concatenate([rng.integers(0, L, 512), [0, L - 1, 0, L - 1, 255, 256, 511, 512]])
+    ys = np.concatenate([rng.integers(0, L, 512), [0, 0, L - 1, L - 1, 87, 88, 175, 176]])
+    with A.Lattice(nx=L, ny=L, tau=v.tau, eps=v.eps, U0=v.U0, T_period=float(v.T), vortex_sign=v.sign,
+                   precision=precision) as g:
+        g.set_state(s.f, s.phi_prev, s.t)
+        f_in, pp_in = g.get_state()
+        del s
+        ref = O.Sim.from_state(op, f_in, pp_in, 2)
+        del f_in
+        fn, ph = ref.step_cells(xs, ys)
+        scale = np.abs(ref.f).max()
+        del ref
+        g.step(1)
+        f, pp = g.get_state()
+        m_state = g.mass()
+        m_step = g.step_mass()
+    got = f[:, ys, xs].T
+    assert np.abs(got - fn).max() <= tol * scale
+    assert np.abs(pp[ys, xs] - ph).max() <= 1e-6       # phi(t) itself is FP32
+    assert m_step == pytest.approx(pp.astype(np.float64).sum(), rel=1e-12)
+    assert m_state == pytest.approx(f.sum(), rel=1e-6)  # f as read back: 16-bit g + FP32 phi
+
+
 @pytest.mark.parametrize("precision", [A.F16DEV, A.BF16DEV])
 def test_dev_phi_readout_matches_state(precision):
     """get_phi returns the moment of the populations get_state returns."""
