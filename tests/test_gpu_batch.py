@@ -84,3 +84,25 @@ def test_batch_rejects_unsupported_lattices():
         A.Batch([dict(nx=65, ny=64)])
     with pytest.raises(A.LbmAceError):
         A.Batch([dict(nx=64, ny=64), dict(nx=64, ny=64, model=A.MODEL_CONSERVATIVE)])
+
+
+def test_full_batch_of_256_lattices_at_sampled_lattices():
+    """The 256-lattice workload of the batch study (73.65M nodes, seeded draws of size,
+    disk, eps, tau, U0 and T), autotuned and stepped as the study runs it; the smallest,
+    the largest and six random lattices are checked against the same lattice alone."""
+    from paper_2203_05230_gb300 import experiments as E
+    specs = E.batch_specs(256)
+    sides = np.array([s["nx"] for s in specs])
+    picks = sorted({int(np.argmin(sides)), int(np.argmax(sides)), 0, 255,
+                    *[int(i) for i in np.random.default_rng(3).choice(256, 4, replace=False)]})
+    with A.Batch(specs) as b:
+        b.autotune(steps_per_trial=1)
+        assert b.t == 0
+        b.step(5)
+        for i in picks:
+            with A.Lattice(precision=A.F32, velocity_kind=A.VEL_SINGLE_VORTEX, **specs[i]) as g:
+                m0 = g.mass()
+                g.step(5)
+                assert np.abs(b.phi(i) - g.phi()).max() <= 1e-6
+                assert b.mass(i) == pytest.approx(g.mass(), rel=1e-6)
+                assert abs(b.mass(i) - m0) <= 1e-5 * m0
