@@ -223,3 +223,24 @@ def test_hybrid_rejects_a_lattice_on_another_stream(net):
         with pytest.raises(A.LbmAceError) as e:
             net.hybrid_advance(a, 1)
         assert e.value.status == A.EINVAL
+
+
+def test_full_size_forward_16_images_256(net):
+    """The benchmark's forward (16 x 256^2 images in one call, the persistent tcgen05
+    launch shape), checked on the first and the last image against the oracle."""
+    B, H, Wd = 16, 256, 256
+    flat, _, _, _, _ = problem(1, 16, 16, seed=1616)   # weights with a visible increment
+    data = W.surrogate_trajectories(B, H, 77)
+    phi = np.stack([d[0] for d in data])
+    u = np.stack([d[1] for d in data])
+    v = np.stack([d[2] for d in data])
+    f32 = lambda a: np.asarray(a, dtype=np.float32).astype(np.float64)
+    phi, u, v = f32(phi), f32(u), f32(v)
+    net.set_params(flat)
+    out = torch.empty((B, H, Wd), dtype=torch.float32, device="cuda")
+    net.forward(dev(phi), dev(u), dev(v), out, B, H, Wd)
+    got = out.cpu().numpy().astype(np.float64)
+    for b in (0, B - 1):
+        emu, _ = S.forward(flat, phi[b:b + 1], u[b:b + 1], v[b:b + 1], emulate=True)
+        assert rel(got[b] - phi[b], emu[0] - phi[b]) < 2e-3
+        assert abs(got[b].sum() - phi[b].sum()) < 2e-6 * phi[b].sum() + 1e-3
