@@ -55,6 +55,7 @@ constexpr int L5_N = 289;             // W5 (288) + b5 (1)
 constexpr float U_SCALE = 20.0f;      // velocity input scale (1 / 0.05)
 constexpr int WG_THREADS = 288;       // 9 warps, one per tap
 constexpr int RED_BLOCKS = 64;        // blocks per image for per-image reductions
+constexpr int MET_BLOCKS = 256;       // blocks of surr_metrics (one field; all SMs at 256^2)
 
 static_assert(OFF_W2 == OFF_W1 + L1_N && OFF_W3 == OFF_W2 + LH_N && OFF_W4 == OFF_W3 + LH_N &&
               OFF_W5 == OFF_W4 + LH_N && OFF_W5 + L5_N == NPARAM, "parameter layout");
@@ -268,44 +269,36 @@ __global__ void __launch_bounds__(256) surr_in_fwd(const float* __restrict__ phi
     for (int k = threadIdx.x; k < 864; k += blockDim.x) wt[k % 27][k / 27] = params[OFF_W1 + k];
     if (threadIdx.x < C) bs[threadIdx.x] = params[OFF_W1 + 864 + threadIdx.x];
     __syncthreads();
-    const int P = B * H * W, pairs = (P + 1) / 2;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < pairs; t += gridDim.x * blockDim.x) {
-        const int p0 = 2 * t;
-        const bool has1 = p0 + 1 < P;
-        float in0[27], in1[27];
-        gather27(phi, u, v, p0, H, W, in0);
-        gather27(phi, u, v, has1 ? p0 + 1 : p0, H, W, in1);
-        float2 in2[27];
-#pragma unroll
-        for (int k = 0; k < 27; ++k) in2[k] = make_float2(in0[k], in1[k]);
+    // one pixel per thread; the packed FP32x2 FMAs take two output channels at once
+    // (each channel summed over the 27 taps in the same order as before)
+    const int P = B * H * W;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < P; p += gridDim.x * blockDim.x) {
+        float in[27];
+        gather27(phi, u, v, p, H, W, in);
 #pragma unroll 1
         for (int cb = 0; cb < 4; ++cb) { // eight output channels per 16-byte store
-            float2 s2[8];                // {pixel 0, pixel 1} of channel cb * 8 + c
+            float2 s2[4];                // channels (cb * 8 + 2 h, cb * 8 + 2 h + 1)
 #pragma unroll
-            for (int c = 0; c < 8; ++c) s2[c] = f2(bs[cb * 8 + c]);
+            for (int h = 0; h < 4; ++h) s2[h] = make_float2(bs[cb * 8 + 2 * h], bs[cb * 8 + 2 * h + 1]);
 #pragma unroll
             for (int k = 0; k < 27; ++k) {
                 const float4 wa = *reinterpret_cast<const float4*>(&wt[k][cb * 8]);
                 const float4 wb = *reinterpret_cast<const float4*>(&wt[k][cb * 8 + 4]);
-                const float w8[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
-#pragma unroll
-                for (int c = 0; c < 8; ++c) s2[c] = __ffma2_rn(f2(w8[c]), in2[k], s2[c]);
+                const float2 x = f2(in[k]);
+                s2[0] = __ffma2_rn(make_float2(wa.x, wa.y), x, s2[0]);
+                s2[1] = __ffma2_rn(make_float2(wa.z, wa.w), x, s2[1]);
+                s2[2] = __ffma2_rn(make_float2(wb.x, wb.y), x, s2[2]);
+                s2[3] = __ffma2_rn(make_float2(wb.z, wb.w), x, s2[3]);
             }
-            unsigned z0w[4], a0w[4], z1w[4], a1w[4];
+            unsigned zw[4], aw[4];
 #pragma unroll
             for (int h = 0; h < 4; ++h) {
-                const float2 ga = gelu2(s2[2 * h]), gb = gelu2(s2[2 * h + 1]);
-                z0w[h] = pack_bf16(s2[2 * h].x, s2[2 * h + 1].x);
-                z1w[h] = pack_bf16(s2[2 * h].y, s2[2 * h + 1].y);
-                a0w[h] = pack_bf16(ga.x, gb.x);
-                a1w[h] = pack_bf16(ga.y, gb.y);
+                const float2 g = gelu2(s2[h]);
+                zw[h] = pack_bf16(s2[h].x, s2[h].y);
+                aw[h] = pack_bf16(g.x, g.y);
             }
-            if (z1) reinterpret_cast<uint4*>(z1 + (size_t)p0 * C)[cb] = make_uint4(z0w[0], z0w[1], z0w[2], z0w[3]);
-            reinterpret_cast<uint4*>(a1 + (size_t)p0 * C)[cb] = make_uint4(a0w[0], a0w[1], a0w[2], a0w[3]);
-            if (has1) {
-                if (z1) reinterpret_cast<uint4*>(z1 + (size_t)(p0 + 1) * C)[cb] = make_uint4(z1w[0], z1w[1], z1w[2], z1w[3]);
-                reinterpret_cast<uint4*>(a1 + (size_t)(p0 + 1) * C)[cb] = make_uint4(a1w[0], a1w[1], a1w[2], a1w[3]);
-            }
+            if (z1) reinterpret_cast<uint4*>(z1 + (size_t)p * C)[cb] = make_uint4(zw[0], zw[1], zw[2], zw[3]);
+            reinterpret_cast<uint4*>(a1 + (size_t)p * C)[cb] = make_uint4(aw[0], aw[1], aw[2], aw[3]);
         }
     }
 }
@@ -1197,6 +1190,12 @@ int red_blocks(int H, int W)
     return (int)std::max(1LL, std::min<long long>(RED_BLOCKS, (n + 255) / 256));
 }
 
+int met_blocks(int H, int W)
+{
+    const long long n = (long long)H * W;
+    return (int)std::max(1LL, std::min<long long>(MET_BLOCKS, (n + 255) / 256));
+}
+
 void free_acts(lbm_ace_net* n)
 {
     for (int l = 0; l < 4; ++l) { cudaFree(n->z[l]); cudaFree(n->a[l]); n->z[l] = n->a[l] = nullptr; }
@@ -1229,7 +1228,7 @@ int ensure_acts(lbm_ace_net* n, long long P, int B, int H = 3, int W = 3)
         NCK(n, cudaMalloc(&n->outb, (size_t)P * sizeof(float)));
         n->cap = P;
     }
-    const int need = B * RED_BLOCKS * 3;
+    const int need = std::max(B * RED_BLOCKS, MET_BLOCKS) * 3;
     if (need > n->rpart_n) {
         cudaFree(n->rpart); cudaFree(n->rpart2);
         n->rpart = n->rpart2 = nullptr;
@@ -1273,7 +1272,7 @@ int run_forward(lbm_ace_net* n, const float* phi, const float* u, const float* v
     // waits for its predecessor with griddepcontrol.wait before reading its output)
     const UGeo g = make_ugeo(B, H, W);
     const long long P = (long long)B * H * W;
-    launch_chain(surr_in_fwd, dim3(grid1((P + 1) / 2, n->sms)), 256, 0, n->stream, phi, u, v,
+    launch_chain(surr_in_fwd, dim3(grid1(P, n->sms)), 256, 0, n->stream, phi, u, v,
                  (const float*)n->params, keep_z ? n->z[0] : nullptr, n->a[0], B, H, W);
     const int grid = (int)std::min<long long>(g.ntiles, n->conv_grid);
     for (int l = 0; l < 3; ++l) {
@@ -1528,7 +1527,7 @@ int lbm_ace_net_metrics(lbm_ace_net* n, const float* phi, int ny, int nx, double
     NetDevice gd(n->dev);
     rc = ensure_acts(n, 0, 1);
     if (rc) return rc;
-    const int rb = red_blocks(ny, nx);
+    const int rb = met_blocks(ny, nx);
     surr_metrics<<<rb, 256, 0, n->stream>>>(phi, ny, nx, n->rpart);
     NCK(n, cudaGetLastError());
     n->hpart.resize(3 * (size_t)rb);
@@ -1606,12 +1605,12 @@ int lbm_ace_hybrid_advance(lbm_ace_ctx* lat, lbm_ace_net* n, long long windows, 
         for (float*& p : n->hyb) NCK(n, cudaMalloc(&p, (size_t)N * sizeof(float)));
         n->hyb_n = N;
     }
-    if (!n->hyb_part) NCK(n, cudaMalloc(&n->hyb_part, (size_t)HYB_DEPTH * 3 * RED_BLOCKS * sizeof(double)));
+    if (!n->hyb_part) NCK(n, cudaMalloc(&n->hyb_part, (size_t)HYB_DEPTH * 3 * MET_BLOCKS * sizeof(double)));
     float* ring[NB];
     for (int k = 0; k < NB; ++k) ring[k] = n->hyb[k];
     float* u = n->hyb[NB];
     float* v = n->hyb[NB + 1];
-    const int rb = red_blocks(ny, nx);
+    const int rb = met_blocks(ny, nx);
 #define LAT(call) do { const int r_ = (call); if (r_) return nfail(n, r_, "lattice: %s", lbm_ace_last_error(lat)); } while (0)
     lbm_ace_hybrid_stats st;
     std::memset(&st, 0, sizeof st);
