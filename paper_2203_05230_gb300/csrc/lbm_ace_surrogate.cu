@@ -379,7 +379,9 @@ __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.
 // Layers 2-5 on the tensor cores: implicit GEMM, one MMA of M = 128 pixels (one row
 // segment of a tile), N output channels, K = 16 input channels per tap and K-half:
 //   out[p][n] = sum_tap sum_k w[tap][n][k] in[p + off(tap)][k],  off(tap) = (tap/3 - 1, tap%3 - 1).
-// A tile is UR = 4 rows x 128 columns of one image. Its (UR+2) x 130 x 32 halo is staged
+// A tile is R rows x 128 columns of one image (R = UR = 4; R = 2 for a forward too small
+// to give every SM two tiles, so that a CTA pipelines several). Its (R+2) x 130 x 32
+// halo is staged
 // by cp.async as four planes of 16-byte channel chunks, so the window of any tap is a
 // set of core matrices 16 bytes apart along M (SBO 128 bytes per 8 pixels) and one
 // plane apart along K. Weights: [tap][chunk][n][8] (block per tap and chunk).
@@ -400,10 +402,11 @@ __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.
 //   MODE_OUT (N = 16, only n = 0 real): z_5 = acc + b_5 (FP32) and 16 partial sums per
 //               tile (one per epilogue warp) in tsum[16 tile + e].
 enum { MODE_FWD = 0, MODE_DGRAD = 1, MODE_OUT = 2 };
-constexpr int UR = 4, UW = 128, UHR = UR + 2, UHW = UW + 2;
-constexpr int UPX = UHR * UHW;            // halo pixels (780)
-constexpr int UPLANE = UPX * 16;          // bytes of one channel-chunk plane
-constexpr int UHALO = 4 * UPLANE;         // bytes of one halo stage
+constexpr int UR = 4, UW = 128, UHW = UW + 2; // default tile height, tile width, halo width
+// bytes of one channel-chunk plane of an R-row tile's halo ((R + 2) x 130 pixels x 16
+// bytes) and of one halo stage (four planes)
+template <int R> __host__ __device__ constexpr int u_plane() { return (R + 2) * UHW * 16; }
+template <int R> __host__ __device__ constexpr int u_halo() { return 4 * u_plane<R>(); }
 constexpr int U_LOAD_WARPS = 4, U_EPI_WARPS = 16;
 constexpr int UMMA_THREADS = (U_LOAD_WARPS + 1 + U_EPI_WARPS) * 32;
 constexpr int U_TSUM = U_EPI_WARPS;       // partial sums per tile (MODE_OUT)
@@ -414,18 +417,18 @@ struct UGeo {
     long long ntiles;
 };
 
-inline UGeo make_ugeo(int B, int H, int W)
+inline UGeo make_ugeo(int B, int H, int W, int R = UR)
 {
     UGeo g;
     g.B = B; g.H = H; g.W = W;
     g.tx = (W + UW - 1) / UW;
-    g.ty = (H + UR - 1) / UR;
+    g.ty = (H + R - 1) / R;
     g.ntiles = (long long)B * g.tx * g.ty;
     return g;
 }
 
-template <int N>
-constexpr int umma_smem_bytes() { return 9 * 4 * N * 16 + 2 * UHALO; }
+template <int N, int R = UR>
+constexpr int umma_smem_bytes() { return 9 * 4 * N * 16 + 2 * u_halo<R>(); }
 
 __device__ __forceinline__ void mbar_init(unsigned mbar, unsigned count)
 {
@@ -436,7 +439,7 @@ __device__ __forceinline__ void mbar_arrive(unsigned mbar)
     asm volatile("{\n.reg .b64 st;\nmbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(mbar) : "memory");
 }
 
-template <int MODE, int N>
+template <int MODE, int N, int R = UR>
 __global__ void __launch_bounds__(UMMA_THREADS, 1) surr_conv_umma(const bf16* __restrict__ in, const bf16* __restrict__ wu,
                                                                   const float* __restrict__ bias,
                                                                   const bf16* __restrict__ zaux, bf16* __restrict__ out_z,
@@ -445,7 +448,9 @@ __global__ void __launch_bounds__(UMMA_THREADS, 1) surr_conv_umma(const bf16* __
                                                                   int* __restrict__ err)
 {
     constexpr int WBYTES = 9 * 4 * N * 16;
-    constexpr int NSET = UR * N;          // TMEM columns of one accumulator set
+    constexpr int UHR = R + 2;            // halo rows of a tile
+    constexpr int UPLANE = u_plane<R>(), UHALO = u_halo<R>();
+    constexpr int NSET = R * N;           // TMEM columns of one accumulator set
     constexpr int NCOL = 2 * NSET;        // two sets (a power of two >= 32)
     constexpr unsigned IDESC = umma_idesc(UW, N);
     extern __shared__ __align__(128) unsigned char smem[];
@@ -496,7 +501,7 @@ __global__ void __launch_bounds__(UMMA_THREADS, 1) surr_conv_umma(const bf16* __
             if (k >= 2 && !mbar_wait(b_empty + 8 * s, (unsigned)(((k >> 1) - 1) & 1))) { failed = true; break; }
             const int b = (int)tile / per;
             const int rem = (int)tile - b * per;
-            const int y0 = (rem / g.tx) * UR, x0 = (rem - (rem / g.tx) * g.tx) * UW;
+            const int y0 = (rem / g.tx) * R, x0 = (rem - (rem / g.tx) * g.tx) * UW;
             unsigned char* st = hs + s * UHALO + kc * UPLANE;
             int xo[5];
 #pragma unroll
@@ -528,7 +533,7 @@ __global__ void __launch_bounds__(UMMA_THREADS, 1) surr_conv_umma(const bf16* __
                 const uint64_t a0 = umma_desc(hs_s + (unsigned)(s * UHALO), UPLANE, 128), b0 = umma_desc(ws_s, N * 16, 128);
                 const unsigned acc = tmem + (unsigned)(s * NSET);
 #pragma unroll
-                for (int r = 0; r < UR; ++r)
+                for (int r = 0; r < R; ++r)
 #pragma unroll
                     for (int tap = 0; tap < 9; ++tap)
 #pragma unroll
@@ -544,8 +549,11 @@ __global__ void __launch_bounds__(UMMA_THREADS, 1) surr_conv_umma(const bf16* __
         __syncwarp();
     } else {
         // ---- epilogue
+        // warp e: TMEM lane quarter q4 (fixed by the warp index), tile row r and, when a
+        // tile has fewer than four rows, channel group cg of its row (chunks k4 of 8)
+        constexpr int KPW = R;                           // of the 4 chunks of 8 channels, per warp
         const int e = warp - U_LOAD_WARPS - 1;          // 0 .. 15
-        const int q4 = warp & 3, r = e >> 2;
+        const int q4 = warp & 3, r = (e >> 2) % R, cg = (e >> 2) / R;
         long long k = 0;
         for (long long tile = blockIdx.x; tile < g.ntiles; tile += gridDim.x, ++k) {
             const int s = (int)(k & 1);
@@ -553,23 +561,25 @@ __global__ void __launch_bounds__(UMMA_THREADS, 1) surr_conv_umma(const bf16* __
             tc_fence_after();
             const int b = (int)tile / per;
             const int rem = (int)tile - b * per;
-            const int y = (rem / g.tx) * UR + r, x = (rem - (rem / g.tx) * g.tx) * UW + 32 * q4 + lane;
+            const int y = (rem / g.tx) * R + r, x = (rem - (rem / g.tx) * g.tx) * UW + 32 * q4 + lane;
             const bool valid = y < g.H && x < g.W;
             const size_t p = valid ? ((size_t)b * g.H + y) * g.W + x : 0;
             const unsigned ta = tmem + ((unsigned)(32 * q4) << 16) + (unsigned)(s * NSET + r * N);
             double psum = 0.0;
             if (MODE == MODE_OUT) {
                 unsigned v[8];
-                tmem_ld8(ta, v);
-                tmem_wait_ld();
-                if (valid) {
+                if (cg == 0) { // the one real output channel
+                    tmem_ld8(ta, v);
+                    tmem_wait_ld();
+                }
+                if (valid && cg == 0) {
                     const float z = __uint_as_float(v[0]) + bv[0];
                     z5[p] = z;
                     psum = z;
                 }
             } else {
 #pragma unroll 1
-                for (int k4 = 0; k4 < 4; ++k4) {
+                for (int k4 = cg * KPW; k4 < (cg + 1) * KPW; ++k4) {
                     unsigned v[8];
                     tmem_ld8(ta + (unsigned)(k4 * 8), v);
                     tmem_wait_ld();
@@ -1138,6 +1148,7 @@ struct lbm_ace_net {
     int conv_grid = 0, out_grid = 0, wg_grid = 0, ob_grid = 0, iw_grid = 0;
     int conv_occ = 0, out_occ = 0;  // resident CTAs per SM reported for the tensor-core kernels
     size_t conv_smem = 0, out_smem = 0, wg_smem = 0, ob_smem = 0;
+    size_t conv_smem2 = 0, out_smem2 = 0; // 2-row tiles (small forwards)
     std::vector<double> hpart;
     // hybrid advance: HYB_DEPTH + 1 phase fields (a ring), u, v, and the metric partials of
     // HYB_DEPTH speculative windows
@@ -1207,7 +1218,7 @@ void free_acts(lbm_ace_net* n)
 
 int ensure_acts(lbm_ace_net* n, long long P, int B, int H = 3, int W = 3)
 {
-    const long long nt = make_ugeo(B, H, W).ntiles * U_TSUM;
+    const long long nt = make_ugeo(B, H, W, 2).ntiles * U_TSUM; // the 2-row tiles are the most
     if (nt > n->tsum_n) {
         cudaFree(n->tsum);
         n->tsum = nullptr;
@@ -1270,20 +1281,25 @@ int run_forward(lbm_ace_net* n, const float* phi, const float* u, const float* v
 {
     // the forward chain is launched with programmatic stream serialisation (each kernel
     // waits for its predecessor with griddepcontrol.wait before reading its output)
-    const UGeo g = make_ugeo(B, H, W);
+    // 2-row tiles when 4-row tiles would not give every conv CTA two (a CTA then
+    // pipelines the loads, MMAs and epilogues of several tiles)
+    const bool small = make_ugeo(B, H, W).ntiles < 2LL * n->conv_grid;
+    const UGeo g = make_ugeo(B, H, W, small ? 2 : UR);
     const long long P = (long long)B * H * W;
     launch_chain(surr_in_fwd, dim3(grid1(P, n->sms)), 256, 0, n->stream, phi, u, v,
                  (const float*)n->params, keep_z ? n->z[0] : nullptr, n->a[0], B, H, W);
     const int grid = (int)std::min<long long>(g.ntiles, n->conv_grid);
     for (int l = 0; l < 3; ++l) {
-        launch_chain(surr_conv_umma<MODE_FWD, 32>, dim3(grid), UMMA_THREADS, n->conv_smem, n->stream,
+        launch_chain(small ? surr_conv_umma<MODE_FWD, 32, 2> : surr_conv_umma<MODE_FWD, 32, UR>, dim3(grid),
+                     UMMA_THREADS, small ? n->conv_smem2 : n->conv_smem, n->stream,
                      (const bf16*)n->a[l], (const bf16*)(n->wu + (size_t)l * 9 * C * C),
                      (const float*)(n->params + OFF_W2 + l * LH_N + 9216), (const bf16*)nullptr,
                      keep_z ? n->z[l + 1] : (bf16*)nullptr, n->a[l + 1], (float*)nullptr, (double*)nullptr, g,
                      n->derr);
     }
     const int gout = (int)std::min<long long>(g.ntiles, n->out_grid);
-    launch_chain(surr_conv_umma<MODE_OUT, 16>, dim3(gout), UMMA_THREADS, n->out_smem, n->stream,
+    launch_chain(small ? surr_conv_umma<MODE_OUT, 16, 2> : surr_conv_umma<MODE_OUT, 16, UR>, dim3(gout),
+                 UMMA_THREADS, small ? n->out_smem2 : n->out_smem, n->stream,
                  (const bf16*)n->a[3], (const bf16*)n->w5u, (const float*)(n->params + OFF_W5 + 288),
                  (const bf16*)nullptr, (bf16*)nullptr, (bf16*)nullptr, n->z5, n->tsum, g, n->derr);
     launch_chain(surr_residual, dim3(red_blocks(H, W), B), 256, 0, n->stream, phi, (const float*)n->z5,
@@ -1351,11 +1367,17 @@ int lbm_ace_net_create(int device, void* stream, lbm_ace_net** out)
     // launch shapes: persistent grids of resident CTAs
     n->conv_smem = umma_smem_bytes<32>();
     n->out_smem = umma_smem_bytes<16>();
+    n->conv_smem2 = umma_smem_bytes<32, 2>();
+    n->out_smem2 = umma_smem_bytes<16, 2>();
     n->wg_smem = (size_t)(TH * TW * PS + HPX * PS) * sizeof(bf16);
     n->ob_smem = (size_t)HPX * PS * sizeof(bf16);
     CREATE_CK(cudaFuncSetAttribute(surr_conv_umma<MODE_FWD, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)n->conv_smem));
     CREATE_CK(cudaFuncSetAttribute(surr_conv_umma<MODE_DGRAD, 32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)n->conv_smem));
     CREATE_CK(cudaFuncSetAttribute(surr_conv_umma<MODE_OUT, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)n->out_smem));
+    CREATE_CK(cudaFuncSetAttribute(surr_conv_umma<MODE_FWD, 32, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)n->conv_smem2));
+    CREATE_CK(cudaFuncSetAttribute(surr_conv_umma<MODE_OUT, 16, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)n->out_smem2));
+    CREATE_CK(cudaFuncSetAttribute(surr_conv_umma<MODE_FWD, 32, 2>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    CREATE_CK(cudaFuncSetAttribute(surr_conv_umma<MODE_OUT, 16, 2>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     // the persistent tensor-core kernels want all of the unified L1/shared storage as shared memory
     CREATE_CK(cudaFuncSetAttribute(surr_conv_umma<MODE_FWD, 32>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     CREATE_CK(cudaFuncSetAttribute(surr_conv_umma<MODE_DGRAD, 32>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
