@@ -766,19 +766,46 @@ __device__ __forceinline__ double block_sum_ordered(const double* v, int n, doub
 }
 
 // phi_out = phi + (z_5 - mean(z_5)) per image; tsum holds partial sums of z_5, those of
-// image b being [b * tpi, (b + 1) * tpi).
+// image b being [b * tpi, (b + 1) * tpi). With met (one image), the block also writes
+// the surr_metrics partials of phi_out (met[blk], met[nb + blk], met[2 nb + blk], nb =
+// gridDim.x), recomputing the neighbours' outputs, which round to the same values.
 __global__ void __launch_bounds__(256) surr_residual(const float* __restrict__ phi, const float* __restrict__ z5,
                                                      const double* __restrict__ tsum, int tpi,
-                                                     float* __restrict__ out, int H, int W)
+                                                     float* __restrict__ out, int H, int W, double* __restrict__ met)
 {
     __shared__ double red[256];
     pdl_enter();
     const int b = blockIdx.y;
     const long long HWn = (long long)H * W;
     const double m = block_sum_ordered(tsum + (size_t)b * tpi, tpi, red) / (double)HWn;
+    const size_t base = (size_t)b * HWn;
+    auto o = [&](long long q) { return (float)((double)phi[base + q] + ((double)z5[base + q] - m)); };
+    double sm = 0.0, sp = 0.0, sgr = 0.0;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < HWn; q += (long long)gridDim.x * blockDim.x) {
-        const size_t k = (size_t)b * HWn + q;
-        out[k] = (float)((double)phi[k] + ((double)z5[k] - m));
+        const float fo = o(q);
+        out[base + q] = fo;
+        if (met) { // the terms of surr_metrics, on the stored values
+            const int y = (int)(q / W), x = (int)(q - (long long)y * W);
+            const double f = fo;
+            sm += f;
+            if (f > 0.05 && f < 0.95) {
+                const double gx = 0.5 * ((double)o((long long)y * W + wrap1(x + 1, W)) - (double)o((long long)y * W + wrap1(x - 1, W)));
+                const double gy = 0.5 * ((double)o((long long)wrap1(y + 1, H) * W + x) - (double)o((long long)wrap1(y - 1, H) * W + x));
+                sp += f * (1.0 - f);
+                sgr += sqrt(gx * gx + gy * gy);
+            }
+        }
+    }
+    if (met) {
+        __syncthreads(); // red is reused
+        sm = block_sum(sm, red);
+        sp = block_sum(sp, red);
+        sgr = block_sum(sgr, red);
+        if (threadIdx.x == 0) {
+            met[blockIdx.x] = sm;
+            met[gridDim.x + blockIdx.x] = sp;
+            met[2 * gridDim.x + blockIdx.x] = sgr;
+        }
     }
 }
 
@@ -1276,8 +1303,9 @@ void launch_chain(void (*kernel)(KArgs...), dim3 grid, int threads, size_t smem,
     cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
 
+// met (B = 1 only): also write the surr_metrics partials of `out` (3 x red_blocks(H, W))
 int run_forward(lbm_ace_net* n, const float* phi, const float* u, const float* v, float* out, int B, int H, int W,
-                bool keep_z)
+                bool keep_z, double* met = nullptr)
 {
     // the forward chain is launched with programmatic stream serialisation (each kernel
     // waits for its predecessor with griddepcontrol.wait before reading its output)
@@ -1303,7 +1331,7 @@ int run_forward(lbm_ace_net* n, const float* phi, const float* u, const float* v
                  (const bf16*)n->a[3], (const bf16*)n->w5u, (const float*)(n->params + OFF_W5 + 288),
                  (const bf16*)nullptr, (bf16*)nullptr, (bf16*)nullptr, n->z5, n->tsum, g, n->derr);
     launch_chain(surr_residual, dim3(red_blocks(H, W), B), 256, 0, n->stream, phi, (const float*)n->z5,
-                 (const double*)n->tsum, (int)(g.tx * g.ty * U_TSUM), out, H, W);
+                 (const double*)n->tsum, (int)(g.tx * g.ty * U_TSUM), out, H, W, B == 1 ? met : nullptr);
     NCK(n, cudaGetLastError());
     return LBM_ACE_OK;
 }
@@ -1632,7 +1660,7 @@ int lbm_ace_hybrid_advance(lbm_ace_ctx* lat, lbm_ace_net* n, long long windows, 
     for (int k = 0; k < NB; ++k) ring[k] = n->hyb[k];
     float* u = n->hyb[NB];
     float* v = n->hyb[NB + 1];
-    const int rb = met_blocks(ny, nx);
+    const int rb = red_blocks(ny, nx); // blocks of the residual kernel, which reduces the checks
 #define LAT(call) do { const int r_ = (call); if (r_) return nfail(n, r_, "lattice: %s", lbm_ace_last_error(lat)); } while (0)
     lbm_ace_hybrid_stats st;
     std::memset(&st, 0, sizeof st);
@@ -1652,9 +1680,10 @@ int lbm_ace_hybrid_advance(lbm_ace_ctx* lat, lbm_ace_net* n, long long windows, 
         const int depth = (int)std::min<long long>(run_ahead, windows - w);
         for (int j = 0; j < depth; ++j) {
             LAT(lbm_ace_velocity_device(lat, (double)(t + (long long)j * K) + 0.5 * K, u, v));
-            rc = run_forward(n, ring[(c + j) % NB], u, v, ring[(c + j + 1) % NB], 1, ny, nx, false);
+            // the residual kernel also reduces the window's checks (mass and width)
+            rc = run_forward(n, ring[(c + j) % NB], u, v, ring[(c + j + 1) % NB], 1, ny, nx, false,
+                             n->hyb_part + (size_t)j * 3 * rb);
             if (rc) return rc;
-            surr_metrics<<<rb, 256, 0, n->stream>>>(ring[(c + j + 1) % NB], ny, nx, n->hyb_part + (size_t)j * 3 * rb);
         }
         NCK(n, cudaGetLastError());
         NCK(n, cudaMemcpyAsync(hp.data(), n->hyb_part, (size_t)depth * 3 * rb * sizeof(double), cudaMemcpyDeviceToHost,
