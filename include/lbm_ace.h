@@ -176,7 +176,7 @@ int lbm_ace_set_state(lbm_ace_ctx* c, const double* f, const double* phi_prev, l
 long long lbm_ace_steps_done(const lbm_ace_ctx* c);
 
 /* Launch shape chosen for the fused step: columns and rows per CTA, grid, and the
- * kernel variant (1 to 5, see lbm_ace_params.kernel_variant). Any pointer may be NULL. */
+ * kernel variant (1 to 6, see lbm_ace_params.kernel_variant). Any pointer may be NULL. */
 int lbm_ace_launch_shape(const lbm_ace_ctx* c, int* tile_x, int* rows_per_cta, int* grid_x, int* grid_y,
                          int* kernel_variant);
 
