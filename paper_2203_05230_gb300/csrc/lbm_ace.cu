@@ -558,6 +558,10 @@ __global__ void ace_widen(const float* __restrict__ in, double* __restrict__ out
 template <typename T, class Vel>
 __global__ void ace_velocity(Vel vel, int nx, int ny, float* __restrict__ u_out, float* __restrict__ v_out)
 {
+    // launched with programmatic stream serialisation (its launch and ramp overlap the
+    // previous kernel); it writes only after that kernel has finished
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");
     const long long plane = (long long)nx * ny;
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < plane;
          k += (long long)gridDim.x * blockDim.x) {
@@ -893,16 +897,16 @@ int lbm_ace_velocity_device(lbm_ace_ctx* c, double t, float* u_out, float* v_out
     const int nx = c->p.nx, ny = c->p.ny;
     switch (c->p.velocity_kind) {
     case LBM_ACE_VEL_SINGLE_VORTEX:
-        if (is_f64(c)) ace_velocity<double><<<gr, 256, 0, c->stream>>>(vortex<double>(c, t), nx, ny, u_out, v_out);
-        else ace_velocity<float><<<gr, 256, 0, c->stream>>>(vortex<float>(c, t), nx, ny, u_out, v_out);
+        if (is_f64(c)) launch_pdl(ace_velocity<double, VelVortex<double>>, dim3(gr), 256, c->stream, vortex<double>(c, t), nx, ny, u_out, v_out);
+        else launch_pdl(ace_velocity<float, VelVortex<float>>, dim3(gr), 256, c->stream, vortex<float>(c, t), nx, ny, u_out, v_out);
         break;
     case LBM_ACE_VEL_UNIFORM: {
         VelUniform<double> v; v.ux = c->p.ux; v.uy = c->p.uy;
-        ace_velocity<double><<<gr, 256, 0, c->stream>>>(v, nx, ny, u_out, v_out);
+        launch_pdl(ace_velocity<double, VelUniform<double>>, dim3(gr), 256, c->stream, v, nx, ny, u_out, v_out);
         break;
     }
     default:
-        ace_velocity<double><<<gr, 256, 0, c->stream>>>(planes<double>(c), nx, ny, u_out, v_out);
+        launch_pdl(ace_velocity<double, VelPlanes<double>>, dim3(gr), 256, c->stream, planes<double>(c), nx, ny, u_out, v_out);
         break;
     }
     CK(c, cudaGetLastError());
