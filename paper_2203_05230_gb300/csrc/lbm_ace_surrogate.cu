@@ -1144,7 +1144,7 @@ using namespace surr;
 // ---------------------------------------------------------------------------------
 // Host side.
 
-constexpr int HYB_DEPTH = 8; // surrogate windows run ahead of one host check
+constexpr int HYB_DEPTH = 16; // surrogate windows run ahead of one host check
 
 struct lbm_ace_net {
     int dev = 0;
