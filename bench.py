@@ -327,7 +327,7 @@ def run_ours(args):
 
     e2e = None
     if not args.no_e2e:
-        e2e = run_e2e(args, v, prec, stream, dev, A)
+        e2e = run_e2e(args, v, prec, stream, dev, A, ws)
 
     line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3, "higher_is_better": True,
@@ -362,9 +362,10 @@ def run_ours(args):
     return 0
 
 
-def run_e2e(args, v, prec, stream, dev, A):
+def run_e2e(args, v, prec, stream, dev, A, ws=1):
     """The same metric through the public API with host buffers: phi0 uploaded from
-    pinned host memory, K steps, phi and the mass read back; wall clock."""
+    pinned host memory, K steps, phi and the mass read back; wall clock. With ws > 1
+    ranks, the job's time is the slowest rank's and the value is whole-job."""
     import torch
     from paper_2203_05230_gb300 import workloads as W
     n = args.L * args.L
@@ -381,10 +382,11 @@ def run_e2e(args, v, prec, stream, dev, A):
     dt = time.perf_counter() - t0
     lat.close()
     assert math.isfinite(m)
-    return {"value": n * args.steps / dt / 1e6, "unit": METRIC,
-            "h2d_bytes_per_step": 8 * n / args.steps, "d2h_bytes_per_step": (8 * n + 8) / args.steps,
-            "what": "init from pinned host phi0 + K steps + phi and mass read back, wall clock; "
-                    "bytes per step are the run's totals / K"}
+    dt = max_over_ranks(dt, ws, "cuda")
+    return {"value": job_mlups(ws, n * args.steps, dt), "unit": METRIC,
+            "h2d_bytes_per_step": ws * 8 * n / args.steps, "d2h_bytes_per_step": ws * (8 * n + 8) / args.steps,
+            "what": "init from pinned host phi0 + K steps + phi and mass read back, wall clock (slowest "
+                    "rank); bytes per step are the job's totals / K"}
 
 
 SURR_FLOP_PER_PIXEL = 2 * 9 * (3 * 32 + 3 * 32 * 32 + 32)   # multiply-adds of the five layers x 2
