@@ -245,13 +245,16 @@ def test_mirror_and_transpose_symmetry(model):
     assert np.abs(tr.T - base).max() < 1e-13
 
 
-def test_equilibrium_profile_is_nearly_stationary_and_sharpening_has_the_right_sign():
+@pytest.mark.parametrize("model", [O.MODIFIED, O.CONSERVATIVE])
+def test_equilibrium_profile_is_nearly_stationary_and_sharpening_has_the_right_sign(model):
     """At u = 0 the Eq. 2 profile (reading R1) balances diffusion and sharpening in
     Eq. 8, so a flat slab barely moves; with the sharpening term switched off
-    (eps -> infinity) the same slab diffuses by sqrt(2 M t), which is far larger."""
+    (eps -> infinity) the same slab diffuses by sqrt(2 M t), which is far larger. The
+    profile is the equilibrium of Eq. 1 (reading R8) as well: along it
+    |grad phi| = phi (1 - phi) / eps, the magnitude R8 gives the conservative model."""
     nx, ny, eps = 4, 64, 1.0
     phi0 = W.slab_phi0(nx, ny, 16.0, 47.0, eps)
-    p = O.Params(nx=nx, ny=ny, tau=0.8, eps=eps, vel_kind=O.UNIFORM)
+    p = O.Params(nx=nx, ny=ny, tau=0.8, eps=eps, vel_kind=O.UNIFORM, model=model)
     s = O.Sim(p, phi0).step(3000)
     dev = np.abs(s.phi() - phi0).max()
     q = O.Params(nx=nx, ny=ny, tau=0.8, eps=1e9, vel_kind=O.UNIFORM)
