@@ -14,6 +14,7 @@
 // no cudaMalloc, cudaFree or other allocating routine.
 #include "lbm_ace.h"
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -69,22 +70,75 @@ __global__ void mass_partials_final(const double* __restrict__ partials, int n, 
     if (lane == 0) *out = S + C;
 }
 
-// Device address of the scratch array, resolved once per device with that device
-// current (in host code the array's name is only a host-side stand-in).
+// Identity of the calling thread's current CUDA context (cuCtxGetId: unique for the
+// life of the process, so a context created after cudaDeviceReset gets a new one).
+// The two driver functions come through the runtime, so the library does not link
+// the driver library itself.
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+
+CtxGetCurrentFn g_get_cur = nullptr;
+CtxGetIdFn g_get_id = nullptr;
+std::once_flag g_fn_once;
+
+bool current_ctx_id(unsigned long long* id)
+{
+    std::call_once(g_fn_once, [] {
+        void* f1 = nullptr;
+        void* f2 = nullptr;
+        cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = q1;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+            q1 == cudaDriverEntryPointSuccess && q2 == cudaDriverEntryPointSuccess) {
+            g_get_cur = reinterpret_cast<CtxGetCurrentFn>(f1);
+            g_get_id = reinterpret_cast<CtxGetIdFn>(f2);
+        }
+    });
+    if (!g_get_cur || !g_get_id) return false;
+    CUcontext ctx = nullptr;
+    if (g_get_cur(&ctx) != CUDA_SUCCESS || !ctx) return false;
+    return g_get_id(ctx, id) == CUDA_SUCCESS;
+}
+
+// Device address of the scratch array for the current device. In host code the
+// array's name is only a host-side stand-in, so the address is looked up
+// (cudaGetSymbolAddress, with the device current) at the first call on a device and
+// again whenever that device's context has changed since (after cudaDeviceReset the
+// module is loaded afresh and the array may sit elsewhere).
 std::mutex g_mu;
 double* g_ptr[kMaxDevices] = {};
+unsigned long long g_ctx[kMaxDevices] = {};
 
 cudaError_t scratch_for(int dev, double** out)
 {
+    unsigned long long id = 0;
+    if (!current_ctx_id(&id)) return cudaErrorDeviceUninitialized;
     std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_ptr[dev]) {
+    if (!g_ptr[dev] || g_ctx[dev] != id) {
         void* p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_mass_partials);
         if (e != cudaSuccess) return e;
         g_ptr[dev] = static_cast<double*>(p);
+        g_ctx[dev] = id;
     }
     *out = g_ptr[dev];
     return cudaSuccess;
+}
+
+// True when p is memory the current device `dev` can address as device memory:
+// device allocations of that device, or managed memory. Host memory (pageable or
+// pinned) and other devices' allocations are refused before any launch. A range is
+// checked at its first and last byte, which catches a count that runs past the end
+// of an allocation into unmapped or host memory.
+bool on_device(const void* p, int dev)
+{
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        (void)cudaGetLastError(); // the query's own error; nothing else was pending
+        return false;
+    }
+    if (at.type == cudaMemoryTypeManaged) return true;
+    return at.type == cudaMemoryTypeDevice && at.device == dev;
 }
 
 } // namespace
@@ -96,8 +150,16 @@ extern "C" int lbm_ace_mass_noalloc(const void* values, int precision, long long
     if (count < 0 || count > LBM_ACE_NOALLOC_MAX_COUNT) return LBM_ACE_EINVAL;
     if (count > 0 && !values) return LBM_ACE_EINVAL;
     if (precision != LBM_ACE_F64 && precision != LBM_ACE_F32) return LBM_ACE_EINVAL;
+    // an error left by an earlier call of the caller's stays theirs: no launch, and it
+    // is neither reported as this call's own nor cleared
+    if (cudaPeekAtLastError() != cudaSuccess) return LBM_ACE_ECUDA;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return LBM_ACE_ECUDA;
+    const size_t bytes = (size_t)count * (precision == LBM_ACE_F64 ? sizeof(double) : sizeof(float));
+    if (!on_device(out, dev) || !on_device(reinterpret_cast<const char*>(out) + sizeof(double) - 1, dev))
+        return LBM_ACE_EINVAL;
+    if (count > 0 && (!on_device(values, dev) || !on_device(static_cast<const char*>(values) + bytes - 1, dev)))
+        return LBM_ACE_EINVAL;
     double* partials = nullptr;
     if (scratch_for(dev, &partials) != cudaSuccess) return LBM_ACE_ECUDA;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -107,7 +169,8 @@ extern "C" int lbm_ace_mass_noalloc(const void* values, int precision, long long
             mass_chunks<double><<<chunks, kThreads, 0, s>>>(static_cast<const double*>(values), count, partials);
         else
             mass_chunks<float><<<chunks, kThreads, 0, s>>>(static_cast<const float*>(values), count, partials);
+        if (cudaPeekAtLastError() != cudaSuccess) return LBM_ACE_ECUDA;
     }
     mass_partials_final<<<1, 32, 0, s>>>(partials, chunks, out);
-    return cudaGetLastError() == cudaSuccess ? LBM_ACE_OK : LBM_ACE_ECUDA;
+    return cudaPeekAtLastError() == cudaSuccess ? LBM_ACE_OK : LBM_ACE_ECUDA;
 }

@@ -7,7 +7,10 @@ their own and ask the library for the compensated global mass, which then keeps 
 partial sums in a fixed static device array. This test plays such a caller: it holds
 a lattice's populations in device memory it allocated itself, calls the entry point
 twice in a row through the C ABI, and checks both results against lbm_ace_mass on
-the same populations within the 1e-12 relative bound of the other mass checks.
+the same populations within the 1e-12 relative bound of the other mass checks. It
+also drives the edges of the fixed array (exact multiples of a chunk, more partial
+sums than one warp's lanes, the largest count) on values whose sum is known exactly,
+and checks that host pointers are refused before any device work.
 
 The file is named so that pytest collects it last.
 """
@@ -51,7 +54,33 @@ def test_mass_noalloc_matches_mass_on_two_calls(precision, dtype):
     assert got[2] == pytest.approx(math.fsum(f.astype(dtype).ravel()[:n].astype(np.float64)), rel=1e-12)
 
 
-def test_mass_noalloc_rejects_bad_sizes_without_device_work():
+@pytest.mark.parametrize("count", [2 * A.NOALLOC_CHUNK, 100 * A.NOALLOC_CHUNK + 123, A.NOALLOC_MAX_COUNT])
+def test_mass_noalloc_edges_of_the_scratch_array(count):
+    """Values k mod 1021 times 2^-10 are exact in FP32 and so are all their partial sums
+    in FP64 (at most 2^38 units of 2^-10), so the sum is known exactly from integer
+    arithmetic. Counts: an exact multiple of the chunk, more partial sums than the 32
+    lanes of the final warp, and the largest count (4096 partial sums, 1 GiB of FP32)."""
+    torch = pytest.importorskip("torch")
+    dev = torch.device("cuda", 0)
+    k = torch.arange(count, dtype=torch.int64, device=dev)
+    vals = ((k % 1021).to(torch.float32) * (1.0 / 1024.0)).contiguous()
+    del k
+    q, r = divmod(count, 1021)
+    exact_units = q * (1020 * 1021 // 2) + r * (r - 1) // 2
+    expect = exact_units / 1024.0
+    out = torch.full((2,), float("nan"), dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for j in range(2):
+        assert A.lbm_ace_mass_noalloc(vals.data_ptr(), A.F32, count, out.data_ptr() + 8 * j,
+                                      stream.cuda_stream) == A.OK
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    assert got[0] == expect and got[1] == expect
+    del vals
+    torch.cuda.empty_cache()
+
+
+def test_mass_noalloc_rejects_bad_arguments_without_device_work():
     pytest.importorskip("torch")
     import torch
     out = torch.zeros(1, dtype=torch.float64, device="cuda")
@@ -61,6 +90,24 @@ def test_mass_noalloc_rejects_bad_sizes_without_device_work():
     assert A.lbm_ace_mass_noalloc(0, A.F64, 16, out.data_ptr()) == A.EINVAL
     assert A.lbm_ace_mass_noalloc(vals.data_ptr(), A.F64, 16, 0) == A.EINVAL
     assert A.lbm_ace_mass_noalloc(vals.data_ptr(), A.F16DEV, 16, out.data_ptr()) == A.EINVAL
+    # host memory, pageable and pinned, for either pointer
+    host_vals = np.ones(16)
+    host_out = np.zeros(1)
+    pinned = torch.zeros(16, dtype=torch.float64).pin_memory()
+    assert A.lbm_ace_mass_noalloc(host_vals.ctypes.data, A.F64, 16, out.data_ptr()) == A.EINVAL
+    assert A.lbm_ace_mass_noalloc(vals.data_ptr(), A.F64, 16, host_out.ctypes.data) == A.EINVAL
+    assert A.lbm_ace_mass_noalloc(pinned.data_ptr(), A.F64, 16, out.data_ptr()) == A.EINVAL
+    assert A.lbm_ace_mass_noalloc(vals.data_ptr(), A.F64, 16, pinned.data_ptr()) == A.EINVAL
+    assert host_out[0] == 0.0
+    torch.cuda.synchronize()
+    assert out.item() == 0.0
+    # a count of zero writes 0 without reading `values`
+    out.fill_(float("nan"))
     assert A.lbm_ace_mass_noalloc(vals.data_ptr(), A.F64, 0, out.data_ptr()) == A.OK
     torch.cuda.synchronize()
     assert out.item() == 0.0
+    # the context is still usable: a valid call after all the refusals
+    vals.fill_(0.25)
+    assert A.lbm_ace_mass_noalloc(vals.data_ptr(), A.F64, 16, out.data_ptr()) == A.OK
+    torch.cuda.synchronize()
+    assert out.item() == 4.0
