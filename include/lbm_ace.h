@@ -119,7 +119,8 @@ typedef struct lbm_ace_params {
     void* stream;        /* cudaStream_t for all device work; NULL = the legacy default stream */
     int rows_per_cta;    /* launch shape of the fused step: rows each CTA marches over;
                             0 selects a default for the lattice size and the device */
-    int kernel_variant;  /* fused step kernel: 0 = automatic (4 for even nx, else 1), 1 = direct global
+    int kernel_variant;  /* fused step kernel: 0 = automatic (FP32 with nx a multiple of 4 and at
+                            most 2^23 nodes: 8; else 4 for even nx, else 1), 1 = direct global
                             loads with a CTA-wide row barrier, 2 = rows staged in shared
                             memory by bulk copies (needs nx * element size a multiple of
                             16 bytes), 3 = independent 32-column warps with loads issued a
@@ -127,9 +128,13 @@ typedef struct lbm_ace_params {
                             stores (needs an even nx), 6 = two steps per launch with the
                             intermediate populations in shared memory (FP32, even nx, no
                             velocity callback; an odd step count ends with one variant-4
-                            step; keeps a second phi plane). All give bit-identical results.
-                            The 16-bit deviation storage has its own kernel (reported as 5)
-                            and takes 0 here. */
+                            step; keeps a second phi plane), 8 = four columns per thread in
+                            independent 128-column warp strips (FP32, nx a multiple of 4).
+                            All give bit-identical results.
+                            The 16-bit deviation storage has two kernels of its own, also
+                            bit-identical: 5 = two columns per thread (even nx), 7 = four
+                            columns per thread (nx a multiple of 4); 0 picks 7 when it
+                            applies, else 5. */
 } lbm_ace_params;
 
 typedef struct lbm_ace_ctx lbm_ace_ctx; /* opaque; owns its device buffers */
@@ -176,7 +181,7 @@ int lbm_ace_set_state(lbm_ace_ctx* c, const double* f, const double* phi_prev, l
 long long lbm_ace_steps_done(const lbm_ace_ctx* c);
 
 /* Launch shape chosen for the fused step: columns and rows per CTA, grid, and the
- * kernel variant (1 to 6, see lbm_ace_params.kernel_variant). Any pointer may be NULL. */
+ * kernel variant (1 to 8, see lbm_ace_params.kernel_variant). Any pointer may be NULL. */
 int lbm_ace_launch_shape(const lbm_ace_ctx* c, int* tile_x, int* rows_per_cta, int* grid_x, int* grid_y,
                          int* kernel_variant);
 
@@ -241,20 +246,43 @@ typedef struct lbm_ace_batch lbm_ace_batch;
  * params[0]. */
 int lbm_ace_batch_init(const lbm_ace_params* params, int count, lbm_ace_batch** out);
 
-/* Advance every lattice by n >= 0 steps: n replays of the captured {step, advance}
- * graph. Asynchronous on the batch's stream. */
+/* Advance the batch's clock by n >= 0 steps: n replays of the captured {step, advance}
+ * graph. A lattice advances while the clock is below its end step (lbm_ace_batch_set_ends;
+ * by default it has none) and then keeps its state; retired lattices' tiles leave the
+ * persistent kernel's work list, on the device. Asynchronous on the batch's stream. */
 int lbm_ace_batch_step(lbm_ace_batch* b, long long n);
 
 /* The same n steps as one ordinary launch per lattice per step (the single-lattice
  * column-pair kernel in the launch shape the single-lattice library picks, host-side
- * loop): the baseline a batch is compared with. Synchronous. */
+ * loop, lattices past their end skipped): a baseline a batch is compared with.
+ * Synchronous. */
 int lbm_ace_batch_step_sequential(lbm_ace_batch* b, long long n);
 
+/* The same n steps as one launch per lattice per step, all launches of a step captured
+ * in one CUDA graph with the batch's own tiles and device-side phases: the baseline
+ * without host launch overhead, so that a comparison isolates what the persistent
+ * kernel's shared work list gains. Asynchronous on the batch's stream. */
+int lbm_ace_batch_step_per_lattice(lbm_ace_batch* b, long long n);
+
+/* Per-lattice end steps for uneven runs: lattice i advances while the batch's clock t <
+ * end_steps[i] (a negative entry: no end). NULL sets each lattice's end to its period
+ * T_period rounded to an integer, the time at which the single-vortex benchmark
+ * (Section 3) compares the shape with the initial one. Every end must be >= the current
+ * clock. Rebuilds the work list (latest end first) and drops the captured graphs. */
+int lbm_ace_batch_set_ends(lbm_ace_batch* b, const long long* end_steps);
+
+/* Steps lattice i has taken: min(clock, its end); -1 for a bad argument. */
+long long lbm_ace_batch_lattice_steps(const lbm_ace_batch* b, int i);
+
+/* Lattices and work-list tiles still active at the current clock. */
+int lbm_ace_batch_active(const lbm_ace_batch* b, int* lattices, int* tiles);
+
 /* Choose the tile height of each lattice size by coordinate descent over {8, 16, 32,
- * 64, 128, 256}, timing steps_per_trial batch steps per trial with CUDA events; the
- * lattices' states and time are saved before and restored after the trials. Writes
- * the chosen heights to rows_out[count] when not NULL. Allocates a copy of the state
- * for the duration of the call. */
+ * 64, 128, 256}, then the persistent grid's CTAs per SM (1 up to the occupancy limit),
+ * timing steps_per_trial batch steps per trial with CUDA events; the lattices' states
+ * and time are saved before and restored after the trials. Writes the chosen heights
+ * to rows_out[count] when not NULL (the grid is reported by lbm_ace_batch_info).
+ * Allocates a copy of the state for the duration of the call. */
 int lbm_ace_batch_autotune(lbm_ace_batch* b, int steps_per_trial, int* rows_out);
 
 /* phi(x, t) of lattice i (host out[count], count == nx*ny of that lattice). Synchronous. */
@@ -278,10 +306,14 @@ void lbm_ace_batch_destroy(lbm_ace_batch* b); /* NULL-safe */
  * synchronisation that cudaMalloc/cudaFree may bring. They pass their own buffers:
  *   values   device address of `count` values, FP64 (precision LBM_ACE_F64) or FP32
  *            (LBM_ACE_F32), e.g. the 9 population planes of a lattice or a phi field;
- *   out      device address of one double that receives the sum (the same
- *            compensated, fixed-order summation as lbm_ace_mass; 0 for count == 0);
+ *   out      device address of one double that receives the sum (0 for count == 0):
+ *            the same Neumaier-compensated algorithm as lbm_ace_mass, in a fixed but
+ *            different order, so the two agree to about 1e-15 relative, not bitwise;
  *   stream   cudaStream_t of the current device (NULL: legacy default stream).
- * The work is asynchronous on `stream` and runs on the current CUDA device.
+ * The work is asynchronous on `stream` and runs on the current CUDA device. Both
+ * pointers must be device memory of the current device (or managed memory); a host
+ * pointer (pageable or pinned), another device's buffer, or a range whose last byte
+ * is not such memory returns LBM_ACE_EINVAL before any launch.
  * Scratch: the per-chunk partial sums live in a fixed array of static device memory
  * inside the library, LBM_ACE_NOALLOC_MAX_PARTIALS doubles (32 KiB), present on every
  * GPU that loads the library until the process exits. Each call overwrites the slots
@@ -289,11 +321,14 @@ void lbm_ace_batch_destroy(lbm_ace_batch* b); /* NULL-safe */
  * array, calls whose work can overlap on the GPU (other streams, other threads)
  * race and may return wrong sums: order them on one stream or synchronise.
  * The first call on a device looks up the array's device address for that device
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * (cudaGetSymbolAddress); make that first call before any stream capture. The lookup
+ * is repeated when the device's context has changed (after cudaDeviceReset), so make
+ * the first call after a reset before any capture too.
  * Limits: count <= LBM_ACE_NOALLOC_MAX_COUNT (268,435,456 values); a larger count,
  * a NULL pointer or another precision returns LBM_ACE_EINVAL without device work.
- * Calls no cudaMalloc, cudaFree or other allocating routine. Returns LBM_ACE_ECUDA
- * when a launch or the address lookup fails. */
+ * Calls no cudaMalloc, cudaFree or other allocating routine. Returns LBM_ACE_ECUDA,
+ * without launching, when a CUDA error from earlier work is already pending (the error
+ * is left pending for its owner), and when a launch or the address lookup fails. */
 #define LBM_ACE_NOALLOC_CHUNK 65536
 #define LBM_ACE_NOALLOC_MAX_PARTIALS 4096
 #define LBM_ACE_NOALLOC_MAX_COUNT (65536LL * 4096LL)

@@ -89,6 +89,7 @@ template <typename T>
 struct VelVortex { // Eq. 14: u = A sx2[x] s2y[y] c(t), v = -A sy2[y] s2x[x] c(t)
     const T* sx2; const T* s2x; const T* sy2; const T* s2y;
     T amp, ct, ctm1;
+    static constexpr bool row_uniform = true; // rowv does not depend on the column
     struct Col { T sx2, s2x; };
     struct Row { T sy2, s2y; };
     __device__ __forceinline__ Col col(int x) const { return {sx2[x], s2x[x]}; }
@@ -104,6 +105,7 @@ struct VelVortex { // Eq. 14: u = A sx2[x] s2y[y] c(t), v = -A sy2[y] s2x[x] c(t
 template <typename T>
 struct VelUniform {
     T ux, uy;
+    static constexpr bool row_uniform = true;
     struct Col {};
     struct Row {};
     __device__ __forceinline__ Col col(int) const { return {}; }
@@ -118,6 +120,7 @@ template <typename T>
 struct VelPlanes { // device FP64 planes of u(t), v(t), u(t-1), v(t-1)
     const double* u; const double* v; const double* up; const double* vp;
     int nx;
+    static constexpr bool row_uniform = false;
     struct Col {};
     struct Row { T u, v, up, vp; };
     __device__ __forceinline__ Col col(int) const { return {}; }
@@ -587,21 +590,116 @@ __global__ void __launch_bounds__(RED_THREADS) ace_sum_partials(const T* __restr
     if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
 }
 
-// Final sum of n partials by one warp: per-lane compensated sums over a strided
-// subset, then lane 0 combines the 32 (sum, compensation) pairs in lane order.
-static __global__ void ace_finalize(const double* __restrict__ part, int n, double* __restrict__ out)
+// Running sum of FP32 values in FP32 parts, two lanes at once: hi collects the values
+// rounded to multiples of 2^-16 (for |v| < 64, (v + 192) - 192 is that rounding and is
+// exact; a sum of such multiples is exact in FP32 while it stays below 256 in
+// magnitude), lo the remainders v - hi (exact, below 2^-17 in magnitude), whose own
+// FP32 sum carries the only rounding, ~1e-14 of the total. Callers flush hi and lo to
+// FP64 before hi can reach 256. It keeps per-value reductions on the FP32 pipes: GB300
+// runs FP64 at 1/64 of the FP32 rate.
+__device__ __forceinline__ void split_add2(float2& hi, float2& lo, float2 v)
 {
-    const int lane = threadIdx.x;
-    double s = 0.0, c = 0.0;
-    for (int k = lane; k < n; k += 32) neumaier(s, c, part[k]);
-    double S = 0.0, C = 0.0;
-    for (int j = 0; j < 32; ++j) {
-        const double sj = __shfl_sync(0xffffffffu, s, j);
-        const double cj = __shfl_sync(0xffffffffu, c, j);
-        neumaier(S, C, sj);
-        neumaier(S, C, cj);
+    const float2 h = __fadd2_rn(__fadd2_rn(v, make_float2(192.0f, 192.0f)), make_float2(-192.0f, -192.0f));
+    hi = __fadd2_rn(hi, h);
+    lo = __fadd2_rn(lo, __fadd2_rn(v, make_float2(-h.x, -h.y)));
+}
+
+__device__ __forceinline__ double split_flush(float2& hi, float2& lo)
+{
+    const double s = ((double)hi.x + (double)hi.y) + ((double)lo.x + (double)lo.y);
+    hi = lo = make_float2(0.0f, 0.0f);
+    return s;
+}
+
+// Mass accumulator of one thread over groups of four FP32 values: groups whose values
+// are all below 2 in magnitude (every population and phi of a lattice in practice) go
+// through split_add2 and are flushed every 32 groups (|hi| < 128); any other group is
+// added in FP64.
+struct MassAcc4 {
+    float2 hi = make_float2(0.0f, 0.0f), lo = make_float2(0.0f, 0.0f);
+    double d = 0.0;
+    int n = 0;
+    __device__ __forceinline__ void add(float4 q)
+    {
+        const float m = fmaxf(fmaxf(fabsf(q.x), fabsf(q.y)), fmaxf(fabsf(q.z), fabsf(q.w)));
+        if (m < 2.0f) {
+            split_add2(hi, lo, make_float2(q.x, q.y));
+            split_add2(hi, lo, make_float2(q.z, q.w));
+            if (++n == 32) {
+                d += split_flush(hi, lo);
+                n = 0;
+            }
+        } else {
+            d += ((double)q.x + (double)q.y) + ((double)q.z + (double)q.w);
+        }
     }
-    if (lane == 0) out[0] = S + C;
+    __device__ __forceinline__ double total() { return d + split_flush(hi, lo); }
+};
+
+// Fixed-order CTA sum of one double per thread into part[blockIdx.x].
+__device__ __forceinline__ void block_sum_to(double v, double* sh, double* part)
+{
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int h = RED_THREADS / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) sh[threadIdx.x] += sh[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+// Partial sums of n FP32 values (16-byte aligned) for the global mass: 16-byte loads,
+// MassAcc4 per thread over a fixed strided subset of the groups of four, the n % 4 last
+// values in FP64 by the first threads of CTA 0, then a fixed tree per CTA.
+// Deterministic, bound by HBM bandwidth rather than by the FP64 pipe.
+static __global__ void __launch_bounds__(RED_THREADS) ace_sum_partials_f32(const float* __restrict__ v, long long n,
+                                                                           double* __restrict__ part)
+{
+    __shared__ double sh[RED_THREADS];
+    const float4* v4 = reinterpret_cast<const float4*>(v);
+    const long long n4 = n >> 2;
+    const long long stride = (long long)gridDim.x * RED_THREADS;
+    MassAcc4 acc;
+    long long k = blockIdx.x * (long long)RED_THREADS + threadIdx.x;
+    for (; k + 3 * stride < n4; k += 4 * stride) { // four independent 16-byte loads in flight
+        const float4 q0 = v4[k], q1 = v4[k + stride], q2 = v4[k + 2 * stride], q3 = v4[k + 3 * stride];
+        acc.add(q0);
+        acc.add(q1);
+        acc.add(q2);
+        acc.add(q3);
+    }
+    for (; k < n4; k += stride) acc.add(v4[k]);
+    double s = acc.total();
+    if (blockIdx.x == 0 && threadIdx.x < (n & 3)) s += (double)v[4 * n4 + threadIdx.x];
+    block_sum_to(s, sh, part);
+}
+
+// Final sum of n partials by one CTA of RED_THREADS threads: each thread a compensated
+// sum over a fixed strided subset, then a fixed pairwise tree in shared memory whose
+// nodes add two (sum, compensation) pairs with an error-free two-sum of the sums. Fixed
+// order, so deterministic; every level runs in parallel (a single warp summing a few
+// thousand partials one after another spent tens of microseconds in FP64 latencies).
+static __global__ void __launch_bounds__(RED_THREADS) ace_finalize(const double* __restrict__ part, int n,
+                                                                   double* __restrict__ out)
+{
+    __shared__ double ss[RED_THREADS], sc[RED_THREADS];
+    double s = 0.0, c = 0.0;
+    for (int k = threadIdx.x; k < n; k += RED_THREADS) neumaier(s, c, part[k]);
+    ss[threadIdx.x] = s;
+    sc[threadIdx.x] = c;
+    __syncthreads();
+    for (int h = RED_THREADS / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) {
+            const double a = ss[threadIdx.x], b = ss[threadIdx.x + h];
+            const double t = a + b;
+            const double bp = t - a;
+            const double err = (a - (t - bp)) + (b - bp); // two-sum: a + b = t + err exactly
+            ss[threadIdx.x] = t;
+            sc[threadIdx.x] += sc[threadIdx.x + h] + err;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = ss[0] + sc[0];
 }
 
 } // namespace lbmace

@@ -9,6 +9,8 @@
 #include "ace_step_warp.cuh"
 #include "ace_step_pair.cuh"
 #include "ace_step_dev.cuh"
+#include "ace_step_dev4.cuh"
+#include "ace_step_quad.cuh"
 #include "ace_step_tb2.cuh"
 
 #include <cuda_runtime.h>
@@ -66,7 +68,7 @@ struct lbm_ace_ctx {
     int variant = 1;        // 1: ace_step (direct loads), 2: ace_step_bulk
     int tile_x = TILE_X;
     size_t smem = 0;        // dynamic shared memory of the chosen step kernel
-    int* dev_err = nullptr; // set by a kernel whose bounded wait gave up
+    int* dev_err = nullptr; // set by a kernel whose bounded wait gave up (inside the result block)
     std::string err;
 };
 
@@ -155,12 +157,13 @@ constexpr int BULK_STAGES = 6;
 // Launch with programmatic stream serialisation: the kernel may start while the previous
 // kernel in the stream drains; it waits (griddepcontrol.wait) before reading the state.
 template <typename... KArgs, typename... Args>
-void launch_pdl(void (*kernel)(KArgs...), dim3 grid, int threads, cudaStream_t stream, Args&&... args)
+void launch_pdl_smem(void (*kernel)(KArgs...), dim3 grid, int threads, size_t smem, cudaStream_t stream,
+                     Args&&... args)
 {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = grid;
     cfg.blockDim = dim3(threads);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = stream;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -168,6 +171,12 @@ void launch_pdl(void (*kernel)(KArgs...), dim3 grid, int threads, cudaStream_t s
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
+
+template <typename... KArgs, typename... Args>
+void launch_pdl(void (*kernel)(KArgs...), dim3 grid, int threads, cudaStream_t stream, Args&&... args)
+{
+    launch_pdl_smem(kernel, grid, threads, 0, stream, std::forward<Args>(args)...);
 }
 
 template <typename T, int MODEL, class Vel>
@@ -181,6 +190,10 @@ void launch_step_k(lbm_ace_ctx* c, const Vel& vel)
         ace_step_warp<T, MODEL, Vel><<<grid, TILE_X, 0, c->stream>>>(make_args<T>(c), vel);
     else if (c->variant == 4 || c->variant == 6) // variant 6: a lone step (odd count) is one pair step
         launch_pdl(ace_step_pair<T, MODEL, Vel>, grid, PAIR_THREADS, c->stream, make_args<T>(c), vel);
+    else if (c->variant == 8) {
+        if constexpr (sizeof(T) == 4)
+            launch_pdl_smem(ace_step_quad<MODEL, Vel>, grid, Q32_THREADS, c->smem, c->stream, make_args<T>(c), vel);
+    }
     else
         ace_step<T, MODEL, Vel><<<grid, TILE_X, 0, c->stream>>>(make_args<T>(c), vel);
 }
@@ -222,7 +235,10 @@ void launch_dev_k(lbm_ace_ctx* c, const Vel& vel)
 {
     dim3 grid(c->grid_x, c->grid_y);
     StepArgs<float> a = make_args<float>(c);
-    launch_pdl(ace_step_dev<S, MODEL, Vel>, grid, PAIR_THREADS, c->stream, make_dev<S>(c), a, vel);
+    if (c->variant == 7)
+        launch_pdl_smem(ace_step_dev4<S, MODEL, Vel>, grid, QUAD_THREADS, c->smem, c->stream, make_dev<S>(c), a, vel);
+    else
+        launch_pdl(ace_step_dev<S, MODEL, Vel>, grid, PAIR_THREADS, c->stream, make_dev<S>(c), a, vel);
 }
 
 template <typename S, int MODEL>
@@ -389,6 +405,16 @@ int occupancy_k(lbm_ace_ctx* c, int* blocks)
         c->smem = 0;
         c->tile_x = PAIR_COLS;
         CK(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, ace_step_pair<T, MODEL, Vel>, PAIR_THREADS, 0));
+    } else if (c->variant == 8) {
+        if constexpr (sizeof(T) == 4) {
+            auto k = ace_step_quad<MODEL, Vel>;
+            c->smem = sizeof(Quad32Smem);
+            c->tile_x = Q32_COLS;
+            CK(c, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem));
+            CK(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k, Q32_THREADS, c->smem));
+        } else {
+            return fail(c, LBM_ACE_EINVAL, "kernel_variant 8 is FP32 only");
+        }
     } else if (c->variant == 6) {
         if constexpr (sizeof(T) == 4) {
             auto k = ace_step_tb2<MODEL, Vel>;
@@ -420,6 +446,14 @@ int occupancy_m(lbm_ace_ctx* c, int* blocks)
 template <typename S, int MODEL, class Vel>
 int occupancy_dev_k(lbm_ace_ctx* c, int* blocks)
 {
+    if (c->variant == 7) {
+        auto k = ace_step_dev4<S, MODEL, Vel>;
+        c->smem = sizeof(QuadSmem);
+        c->tile_x = QUAD_COLS;
+        CK(c, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem));
+        CK(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k, QUAD_THREADS, c->smem));
+        return LBM_ACE_OK;
+    }
     c->smem = 0;
     c->tile_x = PAIR_COLS;
     CK(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, ace_step_dev<S, MODEL, Vel>, PAIR_THREADS, 0));
@@ -481,20 +515,32 @@ int check_device_error(lbm_ace_ctx* c);
 
 int finalize_sum(lbm_ace_ctx* c, const double* part, int n, double* out)
 {
-    ace_finalize<<<1, 32, 0, c->stream>>>(part, n, c->result);
+    // one copy brings back the sum and the wait-failure flag that sits right after it
+    ace_finalize<<<1, RED_THREADS, 0, c->stream>>>(part, n, c->result);
     CK(c, cudaGetLastError());
-    CK(c, cudaMemcpyAsync(out, c->result, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    double back[3];
+    CK(c, cudaMemcpyAsync(back, c->result, sizeof back, cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
-    return check_device_error(c);
+    int e;
+    std::memcpy(&e, &back[2], sizeof e);
+    if (e) {
+        CK(c, cudaMemsetAsync(c->dev_err, 0, sizeof(int), c->stream));
+        CK(c, cudaStreamSynchronize(c->stream));
+        return fail(c, LBM_ACE_ETIMEOUT, "a bounded wait in the step kernel gave up; the state is not valid");
+    }
+    *out = back[0];
+    return LBM_ACE_OK;
 }
 
 // After a stream synchronisation: report (and clear) a bounded wait that gave up.
 int check_device_error(lbm_ace_ctx* c)
 {
     int e = 0;
-    CK(c, cudaMemcpy(&e, c->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
+    CK(c, cudaMemcpyAsync(&e, c->dev_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
     if (e) {
-        CK(c, cudaMemset(c->dev_err, 0, sizeof(int)));
+        CK(c, cudaMemsetAsync(c->dev_err, 0, sizeof(int), c->stream));
+        CK(c, cudaStreamSynchronize(c->stream));
         return fail(c, LBM_ACE_ETIMEOUT, "a bounded wait in the step kernel gave up; the state is not valid");
     }
     return LBM_ACE_OK;
@@ -621,7 +667,7 @@ void lbm_ace_destroy(lbm_ace_ctx* c)
     DeviceGuard g(c->dev);
     if (c->stream) cudaStreamSynchronize(c->stream); else cudaDeviceSynchronize();
     void* bufs[] = {c->f[0], c->f[1], c->phi, c->phi_alt, c->phi2[0], c->phi2[1], c->step_part, c->red_part, c->result,
-                    c->scratch, c->dev_err,
+                    c->scratch,
                     c->vel.sx2, c->vel.s2x, c->vel.sy2, c->vel.s2y,
                     c->vel.pu[0], c->vel.pu[1], c->vel.pv[0], c->vel.pv[1]};
     for (void* b : bufs) if (b) cudaFree(b);
@@ -649,16 +695,27 @@ static int init_impl(lbm_ace_ctx* c, const lbm_ace_params* p)
         CK(c, cudaMalloc(&c->phi, n * c->elem));
     }
     if (p->kernel_variant == 6) CK(c, cudaMalloc(&c->phi_alt, n * sizeof(float)));
-    CK(c, cudaMalloc(&c->result, 2 * sizeof(double)));
+    // result block: the reduced sum, a spare double, then the device wait-failure flag
+    CK(c, cudaMalloc(&c->result, 4 * sizeof(double)));
+    c->dev_err = reinterpret_cast<int*>(c->result + 2);
 
-    CK(c, cudaMalloc(&c->dev_err, sizeof(int)));
-    CK(c, cudaMemset(c->dev_err, 0, sizeof(int)));
+    CK(c, cudaMemset(c->result, 0, 4 * sizeof(double)));
 
     // kernel variant: the bulk-copy pipeline needs 16-byte aligned rows
     // automatic choice: column pairs when nx is even (fastest measured on GB300 at
     // 2048^2), else direct loads
-    c->variant = p->kernel_variant != 0 ? p->kernel_variant : (nx % 2 == 0 ? 4 : 1);
-    if (is_dev(c)) c->variant = 5; // the deviation-storage kernel (column pairs)
+    // automatic choice, measured on GB300 (FP32): four columns per thread in warp strips
+    // up to 2^23 nodes (1024^2: 71k against 67k MLUPS for column pairs; 2048^2: 80k against
+    // 79k), column pairs above (4096^2: 82k against 80k), direct loads for odd nx; FP64:
+    // column pairs for even nx
+    if (p->kernel_variant != 0)
+        c->variant = p->kernel_variant;
+    else if (p->precision == LBM_ACE_F32 && nx % 4 == 0 && (long long)nx * ny <= (1LL << 23))
+        c->variant = 8;
+    else
+        c->variant = nx % 2 == 0 ? 4 : 1;
+    // the deviation-storage kernels: four columns per thread when nx allows, else pairs
+    if (is_dev(c)) c->variant = p->kernel_variant != 0 ? p->kernel_variant : (nx % 4 == 0 ? 7 : 5);
 
     // launch shape of the fused step: one wave of resident CTAs when possible
     int occ = 0;
@@ -761,8 +818,14 @@ int lbm_ace_init(const lbm_ace_params* p, lbm_ace_ctx** out)
         return fail(nullptr, LBM_ACE_EINVAL, "precision %d unknown", p->precision);
     if ((p->precision == LBM_ACE_F16DEV || p->precision == LBM_ACE_BF16DEV) && p->nx % 2 != 0)
         return fail(nullptr, LBM_ACE_EINVAL, "16-bit deviation storage needs an even nx (nx = %d)", p->nx);
-    if ((p->precision == LBM_ACE_F16DEV || p->precision == LBM_ACE_BF16DEV) && p->kernel_variant != 0)
-        return fail(nullptr, LBM_ACE_EINVAL, "16-bit deviation storage has one step kernel; kernel_variant must be 0");
+    const bool dev16 = p->precision == LBM_ACE_F16DEV || p->precision == LBM_ACE_BF16DEV;
+    if (dev16 && p->kernel_variant != 0 && p->kernel_variant != 5 && p->kernel_variant != 7)
+        return fail(nullptr, LBM_ACE_EINVAL, "16-bit deviation storage takes kernel_variant 0, 5 or 7 (got %d)",
+                    p->kernel_variant);
+    if (dev16 && p->kernel_variant == 7 && p->nx % 4 != 0)
+        return fail(nullptr, LBM_ACE_EINVAL, "kernel_variant 7 needs nx a multiple of 4 (nx = %d)", p->nx);
+    if (!dev16 && (p->kernel_variant == 5 || p->kernel_variant == 7))
+        return fail(nullptr, LBM_ACE_EINVAL, "kernel_variant %d is for the 16-bit deviation storage", p->kernel_variant);
     if (p->model != LBM_ACE_MODEL_MODIFIED && p->model != LBM_ACE_MODEL_CONSERVATIVE)
         return fail(nullptr, LBM_ACE_EINVAL, "model %d unknown", p->model);
     switch (p->velocity_kind) {
@@ -790,8 +853,10 @@ int lbm_ace_init(const lbm_ace_params* p, lbm_ace_ctx** out)
         return fail(nullptr, LBM_ACE_EINVAL, "disk centre/radius not finite");
     }
     if (p->rows_per_cta < 0) return fail(nullptr, LBM_ACE_EINVAL, "rows_per_cta must be >= 0");
-    if (p->kernel_variant < 0 || p->kernel_variant > 6 || p->kernel_variant == 5)
+    if (p->kernel_variant < 0 || p->kernel_variant > 8)
         return fail(nullptr, LBM_ACE_EINVAL, "kernel_variant %d unknown", p->kernel_variant);
+    if (p->kernel_variant == 8 && (p->precision != LBM_ACE_F32 || p->nx % 4 != 0))
+        return fail(nullptr, LBM_ACE_EINVAL, "kernel_variant 8 needs FP32 and nx a multiple of 4 (nx = %d)", p->nx);
     if (p->kernel_variant == 6 && (p->precision != LBM_ACE_F32 || p->nx % 2 != 0 ||
                                    p->velocity_kind == LBM_ACE_VEL_CALLBACK))
         return fail(nullptr, LBM_ACE_EINVAL,
@@ -958,7 +1023,7 @@ int lbm_ace_mass(lbm_ace_ctx* c, double* out)
     const unsigned short* gs = (const unsigned short*)c->f[c->cur];
     switch (c->p.precision) {
     case LBM_ACE_F64: ace_sum_partials<double><<<c->n_red_part, RED_THREADS, 0, c->stream>>>((const double*)c->f[c->cur], n9, c->red_part); break;
-    case LBM_ACE_F32: ace_sum_partials<float><<<c->n_red_part, RED_THREADS, 0, c->stream>>>((const float*)c->f[c->cur], n9, c->red_part); break;
+    case LBM_ACE_F32: ace_sum_partials_f32<<<c->n_red_part, RED_THREADS, 0, c->stream>>>((const float*)c->f[c->cur], n9, c->red_part); break;
     case LBM_ACE_F16DEV:
         ace_sum_partials_dev<__half><<<c->n_red_part, RED_THREADS, 0, c->stream>>>(gs, c->phi2[c->pcur], n, c->red_part);
         break;

@@ -28,7 +28,7 @@ MODEL_MODIFIED, MODEL_CONSERVATIVE = 0, 1
 VEL_SINGLE_VORTEX, VEL_UNIFORM, VEL_FIELD, VEL_CALLBACK = 0, 1, 2, 3
 # fused step kernel variant
 KERNEL_AUTO, KERNEL_DIRECT, KERNEL_BULK, KERNEL_WARP, KERNEL_PAIR = 0, 1, 2, 3, 4
-KERNEL_DEV, KERNEL_TWO_STEP = 5, 6
+KERNEL_DEV, KERNEL_TWO_STEP, KERNEL_DEV4, KERNEL_QUAD = 5, 6, 7, 8
 
 VELOCITY_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
@@ -43,12 +43,14 @@ EXPORTS = (
     "lbm_ace_batch_init", "lbm_ace_batch_step", "lbm_ace_batch_step_sequential", "lbm_ace_batch_autotune",
     "lbm_ace_batch_get_phi", "lbm_ace_batch_mass", "lbm_ace_batch_info", "lbm_ace_batch_steps_done",
     "lbm_ace_batch_synchronize", "lbm_ace_batch_last_error", "lbm_ace_batch_destroy",
+    "lbm_ace_batch_step_per_lattice", "lbm_ace_batch_set_ends", "lbm_ace_batch_lattice_steps",
+    "lbm_ace_batch_active",
     "lbm_ace_get_phi_device", "lbm_ace_velocity_device", "lbm_ace_reset_device", "lbm_ace_get_stream",
     "lbm_ace_get_params", "lbm_ace_wait_selftest",
     "lbm_ace_net_create", "lbm_ace_net_set_params", "lbm_ace_net_get_params", "lbm_ace_net_forward",
     "lbm_ace_net_loss_grad", "lbm_ace_net_adam", "lbm_ace_net_gather", "lbm_ace_net_metrics",
     "lbm_ace_net_synchronize", "lbm_ace_net_last_error", "lbm_ace_net_destroy", "lbm_ace_hybrid_advance",
-    "lbm_ace_net_launch_shape",
+    "lbm_ace_net_launch_shape", "lbm_ace_net_wait_selftest",
 )
 NET_WIDTH, NET_K, NET_PARAMS = 32, 16, 28929
 NOALLOC_CHUNK = 65536
@@ -141,9 +143,15 @@ def load(build_if_missing: bool = True):
     L.lbm_ace_batch_last_error.restype = ctypes.c_char_p
     L.lbm_ace_batch_destroy.argtypes = [_P]
     L.lbm_ace_batch_destroy.restype = None
+    L.lbm_ace_batch_step_per_lattice.argtypes = [_P, ctypes.c_longlong]
+    L.lbm_ace_batch_set_ends.argtypes = [_P, ctypes.POINTER(ctypes.c_longlong)]
+    L.lbm_ace_batch_lattice_steps.argtypes = [_P, ctypes.c_int]
+    L.lbm_ace_batch_lattice_steps.restype = ctypes.c_longlong
+    L.lbm_ace_batch_active.argtypes = [_P, _I, _I]
     for name in ("lbm_ace_batch_init", "lbm_ace_batch_step", "lbm_ace_batch_step_sequential",
                  "lbm_ace_batch_autotune", "lbm_ace_batch_get_phi", "lbm_ace_batch_mass",
-                 "lbm_ace_batch_info", "lbm_ace_batch_synchronize"):
+                 "lbm_ace_batch_info", "lbm_ace_batch_synchronize", "lbm_ace_batch_step_per_lattice",
+                 "lbm_ace_batch_set_ends", "lbm_ace_batch_active"):
         getattr(L, name).restype = ctypes.c_int
     for name in ("lbm_ace_params_default", "lbm_ace_init", "lbm_ace_step", "lbm_ace_get_phi",
                  "lbm_ace_mass", "lbm_ace_step_mass", "lbm_ace_get_state", "lbm_ace_set_state",
@@ -170,6 +178,8 @@ def load(build_if_missing: bool = True):
     L.lbm_ace_net_gather.argtypes = [_P, _P, _P, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int, ctypes.c_longlong]
     L.lbm_ace_net_metrics.argtypes = [_P, _P, ctypes.c_int, ctypes.c_int, _D, _D]
     L.lbm_ace_net_synchronize.argtypes = [_P]
+    L.lbm_ace_net_wait_selftest.argtypes = [_P, ctypes.c_longlong]
+    L.lbm_ace_net_wait_selftest.restype = ctypes.c_int
     L.lbm_ace_net_launch_shape.argtypes = [_P] + [ctypes.POINTER(ctypes.c_int)] * 5
     L.lbm_ace_net_launch_shape.restype = ctypes.c_int
     L.lbm_ace_net_last_error.argtypes = [_P]
@@ -425,6 +435,28 @@ class Batch:
     def t(self):
         return int(self._lib.lbm_ace_batch_steps_done(self.h))
 
+    def step_per_lattice(self, n=1):
+        self._check(self._lib.lbm_ace_batch_step_per_lattice(self.h, int(n)))
+        return self
+
+    def set_ends(self, ends=None):
+        """Per-lattice end steps (None: each lattice's T_period rounded; -1: no end)."""
+        if ends is None:
+            self._check(self._lib.lbm_ace_batch_set_ends(self.h, None))
+        else:
+            arr = (ctypes.c_longlong * len(self.shapes))(*[int(e) for e in ends])
+            self._check(self._lib.lbm_ace_batch_set_ends(self.h, arr))
+        return self
+
+    def lattice_steps(self, i):
+        return int(self._lib.lbm_ace_batch_lattice_steps(self.h, int(i)))
+
+    def active(self):
+        """(lattices, tiles) still advancing at the batch's clock."""
+        a, t = ctypes.c_int(), ctypes.c_int()
+        self._check(self._lib.lbm_ace_batch_active(self.h, ctypes.byref(a), ctypes.byref(t)))
+        return a.value, t.value
+
     def synchronize(self):
         self._check(self._lib.lbm_ace_batch_synchronize(self.h))
 
@@ -532,6 +564,13 @@ class Net:
         self._check(self._lib.lbm_ace_net_synchronize(self.h))
 
     synchronize = lbm_ace_net_synchronize
+
+    def lbm_ace_net_wait_selftest(self, limit_cycles: int) -> None:
+        """Run the bounded-wait failure self-test; raises LbmAceError (status ETIMEOUT)
+        when the wait gave up, which is the expected outcome."""
+        self._check(self._lib.lbm_ace_net_wait_selftest(self.h, int(limit_cycles)))
+
+    wait_selftest = lbm_ace_net_wait_selftest
 
     def lbm_ace_hybrid_advance(self, lattice: "Lattice", windows: int, mass_tol: float = 1e-6,
                                width_tol: float = 0.1) -> dict:

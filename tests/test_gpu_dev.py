@@ -26,7 +26,8 @@ def rel_max(a, b):
 
 
 @pytest.mark.parametrize("precision,tol", DEV)
-@pytest.mark.parametrize("nx,ny,model", [(64, 64, 0), (258, 37, 0), (514, 21, 1), (4, 9, 0)])
+@pytest.mark.parametrize("nx,ny,model", [(64, 64, 0), (258, 37, 0), (514, 21, 1), (4, 9, 0), (516, 37, 1),
+                                         (1032, 11, 0)])
 def test_dev_one_step_close_to_oracle(precision, tol, nx, ny, model):
     op = O.Params(nx=nx, ny=ny, tau=0.8, eps=1.0, U0=0.05, T=100.0, sign=-1.0, model=model)
     s = O.Sim(op, W.random_smooth_phi(nx, ny, seed=nx + ny)).step(3)
@@ -133,3 +134,50 @@ def test_dev_rejects_odd_nx_and_variants():
         A.Lattice(nx=65, ny=64, precision=A.F16DEV)
     with pytest.raises(A.LbmAceError):
         A.Lattice(nx=64, ny=64, precision=A.BF16DEV, kernel_variant=1)
+    with pytest.raises(A.LbmAceError):
+        A.Lattice(nx=66, ny=64, precision=A.BF16DEV, kernel_variant=A.KERNEL_DEV4)
+    with pytest.raises(A.LbmAceError):
+        A.Lattice(nx=64, ny=64, precision=A.F32, kernel_variant=A.KERNEL_DEV4)
+
+
+def _vel_kw(kind, nx, ny):
+    if kind == "vortex":
+        return dict(U0=0.05, T_period=60.0, vortex_sign=-1.0)
+    if kind == "uniform":
+        return dict(velocity_kind=A.VEL_UNIFORM, ux=0.03, uy=-0.02)
+    rng = np.random.default_rng(nx * 7 + ny)
+    return dict(velocity_kind=A.VEL_FIELD, u_field=0.04 * rng.uniform(-1, 1, (ny, nx)),
+                v_field=0.04 * rng.uniform(-1, 1, (ny, nx)))
+
+
+@pytest.mark.parametrize("precision", [A.F16DEV, A.BF16DEV])
+@pytest.mark.parametrize("nx,ny,model,vel", [(512, 40, 0, "vortex"), (516, 37, 0, "vortex"), (1028, 19, 1, "uniform"),
+                                             (4, 9, 0, "field"), (8, 3, 0, "vortex"), (264, 130, 0, "field"),
+                                             (2048, 64, 0, "vortex")])
+def test_dev_quad_kernel_is_bit_identical_to_pair_kernel(precision, nx, ny, model, vel):
+    """The four-columns-per-thread kernel (7) and the column-pair kernel (5) do the same
+    arithmetic on the same values: 13 steps from t = 0 (the first step has no time
+    derivative) agree bit for bit, on full and ragged strips, lattices narrower than one
+    quad's strip, every velocity source and both models. The quad kernel's FP64 step
+    mass (summed exactly in FP32 parts) matches the FP64 sum of the phi it wrote."""
+    phi0 = W.random_smooth_phi(nx, ny, seed=nx + 3 * ny)
+    out = []
+    for variant in (A.KERNEL_DEV, A.KERNEL_DEV4):
+        with A.Lattice(nx=nx, ny=ny, model=model, precision=precision, phi0=phi0, kernel_variant=variant,
+                       **_vel_kw(vel, nx, ny)) as g:
+            assert g.launch_shape()[4] == variant
+            g.step(13)
+            f, pp = g.get_state()
+            out.append((f, pp, g.step_mass()))
+    (fa, ppa, ma), (fb, ppb, mb) = out
+    assert np.array_equal(fa, fb) and np.array_equal(ppa, ppb)
+    assert mb == pytest.approx(ppb.astype(np.float64).sum(), rel=1e-13, abs=1e-300)
+    assert ma == pytest.approx(mb, rel=1e-12)
+
+
+@pytest.mark.parametrize("precision", [A.F16DEV, A.BF16DEV])
+def test_dev_default_kernel_choice(precision):
+    with A.Lattice(nx=64, ny=16, precision=precision) as g:
+        assert g.launch_shape()[4] == A.KERNEL_DEV4
+    with A.Lattice(nx=66, ny=16, precision=precision) as g:
+        assert g.launch_shape()[4] == A.KERNEL_DEV

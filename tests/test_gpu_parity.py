@@ -97,6 +97,38 @@ def test_f64_one_step_matches_oracle(nx, ny, variant, model):
     assert rel_max(pp, s.phi_prev) <= ONE_STEP
 
 
+QUAD_SHAPES = [(8, 8), (16, 16), (64, 64), (4, 9), (132, 40), (260, 33), (516, 37), (1028, 19), (384, 3)]
+
+
+@pytest.mark.parametrize("nx,ny", QUAD_SHAPES)
+@pytest.mark.parametrize("model", [A.MODEL_MODIFIED, A.MODEL_CONSERVATIVE])
+@pytest.mark.parametrize("vel", ["vortex", "field"])
+def test_f32_quad_kernel_one_step_matches_oracle(nx, ny, model, vel):
+    """The four-columns-per-thread FP32 kernel (warp strips of 128 columns, ragged and
+    dead strips, lattices narrower than a quad's strip) one step from an oracle state,
+    and bit for bit the column-pair kernel over 10 steps from that state."""
+    op, kw = pair(nx, ny, model=model, vel=vel, precision=A.F32, variant=A.KERNEL_QUAD, seed=nx + ny)
+    s = oracle_state(op, seed=nx * 1000 + ny)
+    out = []
+    for variant in (A.KERNEL_QUAD, A.KERNEL_PAIR):
+        kw["kernel_variant"] = variant
+        with A.Lattice(**kw) as g:
+            assert g.launch_shape()[4] == variant
+            g.set_state(s.f, s.phi_prev, s.t)
+            g.step(1)
+            out.append(g.get_state())
+            g.step(9)
+            out.append(g.get_state() + (g.step_mass(),))
+    f, pp = out[0]
+    nxt = s.copy().step(1)
+    assert rel_max(f, nxt.f) <= 2e-6
+    assert rel_max(pp, nxt.phi_prev) <= 2e-6
+    fq, ppq, mq = out[1]
+    fp_, ppp, _ = out[3]
+    assert np.array_equal(out[0][0], out[2][0]) and np.array_equal(fq, fp_) and np.array_equal(ppq, ppp)
+    assert mq == pytest.approx(ppq.sum(), rel=1e-12)
+
+
 @pytest.mark.parametrize("vel", ["vortex", "uniform", "field"])
 @pytest.mark.parametrize("t0", [0, 1, 57])
 def test_f64_velocity_sources_and_first_step(vel, t0):
@@ -318,10 +350,11 @@ def test_callback_time_dependent_matches_oracle_vortex():
 
 @pytest.mark.parametrize("L,precision", [(2048, A.F32), (512, A.F64), (260, A.F32), (132, A.F64)])
 def test_kernel_variants_are_bit_identical(L, precision):
-    """The three kernel variants do the same arithmetic on the same values: 12 steps of
-    the single vortex agree bit for bit."""
+    """The kernel variants do the same arithmetic on the same values: 12 steps of the
+    single vortex agree bit for bit."""
     out = []
-    for variant in (A.KERNEL_DIRECT, A.KERNEL_BULK, A.KERNEL_WARP, A.KERNEL_PAIR):
+    quad = [A.KERNEL_QUAD] if precision == A.F32 and L % 4 == 0 else []
+    for variant in [A.KERNEL_DIRECT, A.KERNEL_BULK, A.KERNEL_WARP, A.KERNEL_PAIR] + quad:
         with A.vortex_lattice(L, precision=precision, kernel_variant=variant) as g:
             assert g.launch_shape()[4] == variant
             g.step(12)
