@@ -8,8 +8,16 @@
 // kernel) on each, so small lattices that could never fill the GPU alone share it.
 // The step counter t lives on the device; each lattice's phase cos(pi t / T) is
 // computed there, so a captured graph of {step, advance} replays any number of steps
-// without host work. Tile heights come from lbm_ace_batch_autotune (coordinate descent
-// per lattice size, timed with CUDA events on the batch's stream).
+// without host work. Tile heights and the persistent grid's CTAs per SM come from
+// lbm_ace_batch_autotune (coordinate descent, timed with CUDA events on the batch's
+// stream).
+//
+// Uneven runs: each lattice may have its own end step (its period T, Section 3, whose
+// shape at t = T is the benchmark's measure); it advances while t < end and then keeps
+// its state. The work list orders the lattices by end, latest first, so the tiles still
+// active at any t are a prefix of the list; the small per-step kernel that advances the
+// phases also computes that prefix's length for the next step, and the persistent
+// kernel stops pulling work there. Retired lattices cost nothing, in the graph too.
 #include "lbm_ace.h"
 #include "ace_kernels.cuh"
 #include "ace_step_pair.cuh"
@@ -17,6 +25,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -33,6 +42,7 @@ constexpr double kPiB = 3.14159265358979323846;
 constexpr int kMinRows = 8; // smallest tile height the batch is sized for
 
 struct BatchInst {
+    long long end;        // the lattice advances while t < end (LLONG_MAX: no end)
     float* f[2];          // population ping-pong buffers; f[t & 1] holds f*(t - 1)
     float* phi;           // phi(t - 1)
     const float* sx2; const float* s2x; const float* sy2; const float* s2y; // Eq. 14 tables
@@ -43,8 +53,10 @@ struct BatchInst {
 };
 
 struct BatchCtl {
-    int next; // work-item counter of the step in flight
-    int t;    // time of the next step (all lattices advance together)
+    int next;        // work-item counter of the step in flight
+    int t;           // time of the next step (every active lattice advances together)
+    int active;      // tiles of the lattices still active at time t: a prefix of the work list
+    int active_next; // the same for time t + 1, filled in by ace_batch_phase
 };
 
 template <int MODEL>
@@ -76,12 +88,13 @@ __device__ __forceinline__ void batch_tile(const BatchInst& I, float2 ph, int lt
 template <int MODEL>
 __global__ void __launch_bounds__(PAIR_THREADS, 5)
 ace_batch_step(const BatchInst* __restrict__ inst, const float2* __restrict__ phase, const int* __restrict__ tile_inst,
-               int ntiles, BatchCtl* ctl)
+               BatchCtl* ctl)
 {
     __shared__ __align__(16) float chi_s[4][PAIR_COLS + 4];
     __shared__ double red_s[PAIR_THREADS / 32];
     __shared__ int tile_s;
     const int t = ctl->t;
+    const int ntiles = ctl->active;
     for (;;) {
         if (threadIdx.x == 0) tile_s = atomicAdd(&ctl->next, 1);
         __syncthreads();
@@ -93,14 +106,34 @@ ace_batch_step(const BatchInst* __restrict__ inst, const float2* __restrict__ ph
     }
 }
 
-// Phase of Eq. 14 for the next step, t + 1: (cos(pi (t+1) / T), cos(pi t / T)) per lattice.
-__global__ void ace_batch_phase(const BatchCtl* __restrict__ ctl, const BatchInst* __restrict__ inst, int n,
+// One launch per lattice (the per-lattice baseline): CTA b runs tile first + b of the
+// work list, with the same tile code and device-side phases as the persistent kernel.
+template <int MODEL>
+__global__ void __launch_bounds__(PAIR_THREADS, 5)
+ace_batch_one(const BatchInst* __restrict__ inst, const float2* __restrict__ phase, int i, const BatchCtl* ctl)
+{
+    __shared__ __align__(16) float chi_s[4][PAIR_COLS + 4];
+    __shared__ double red_s[PAIR_THREADS / 32];
+    const int t = ctl->t;
+    if (t < inst[i].end) batch_tile<MODEL>(inst[i], phase[i], blockIdx.x, t, chi_s, red_s);
+}
+
+// For the next step, t + 1: the phase of Eq. 14, (cos(pi (t+1) / T), cos(pi t / T)), per
+// lattice, and the length of the active prefix of the work list. end_sorted holds the
+// lattices' ends in work-list order (non-increasing), prefix[j] the tiles of positions
+// 0 .. j; the position j with end_sorted[j] > t + 1 >= end_sorted[j + 1] is the last
+// active one.
+__global__ void ace_batch_phase(BatchCtl* __restrict__ ctl, const BatchInst* __restrict__ inst, int n,
+                                const long long* __restrict__ end_sorted, const int* __restrict__ prefix,
                                 float2* __restrict__ phase)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) {
-        const double t = (double)ctl->t + 1.0;
+        const long long tn = (long long)ctl->t + 1;
+        const double t = (double)tn;
         phase[i] = make_float2((float)cos(kPiB * t / inst[i].T_period), (float)cos(kPiB * (t - 1.0) / inst[i].T_period));
+        if (end_sorted[i] > tn && (i == n - 1 || end_sorted[i + 1] <= tn)) ctl->active_next = prefix[i];
+        if (i == 0 && end_sorted[0] <= tn) ctl->active_next = 0;
     }
 }
 
@@ -108,6 +141,7 @@ __global__ void ace_batch_tick(BatchCtl* ctl)
 {
     ctl->next = 0;
     ctl->t += 1;
+    ctl->active = ctl->active_next;
 }
 
 } // namespace
@@ -125,6 +159,11 @@ struct lbm_ace_batch {
     int ntiles = 0, max_tiles = 0;
     BatchCtl* ctl = nullptr;
     float2* phase = nullptr; // (cos(pi t / T), cos(pi (t-1) / T)) per lattice for the next step
+    std::vector<int> order;  // lattices in work-list order (end descending, then index)
+    long long* d_end_sorted = nullptr; // ends in work-list order
+    int* d_prefix = nullptr;           // tiles of work-list positions 0 .. j
+    std::vector<int> prefix;           // host copy
+    bool per_lattice_graph = false;    // the graph replays the per-lattice baseline
     float* pool = nullptr; size_t pool_elems = 0;
     float* tabs = nullptr;
     double* mass_pool = nullptr;
@@ -133,7 +172,7 @@ struct lbm_ace_batch {
     double* red_part = nullptr; int n_red = 0;
     double* result = nullptr;
     double* scratch = nullptr; size_t scratch_elems = 0;
-    int grid = 0;
+    int grid = 0, grid_max = 0; // persistent CTAs (tuned), and SMs x resident CTAs
     bool own_stream = false;
     long long t = 0;
     cudaGraph_t graph = nullptr;
@@ -177,7 +216,13 @@ void drop_graph(lbm_ace_batch* b)
 int build_tiles(lbm_ace_batch* b)
 {
     b->tile_inst.clear();
-    for (int i = 0; i < b->n; ++i) {
+    b->order.resize(b->n);
+    for (int i = 0; i < b->n; ++i) b->order[i] = i;
+    std::stable_sort(b->order.begin(), b->order.end(), [&](int x, int y) { return b->inst[x].end > b->inst[y].end; });
+    b->prefix.assign(b->n, 0);
+    std::vector<long long> ends(b->n);
+    for (int j = 0; j < b->n; ++j) {
+        const int i = b->order[j];
         BatchInst& I = b->inst[i];
         // heights below kMinRows would need more mass partials than were allocated
         I.rows = std::max(std::min(kMinRows, I.ny), std::min(I.rows, I.ny));
@@ -185,12 +230,16 @@ int build_tiles(lbm_ace_batch* b)
         I.tiles_y = (I.ny + I.rows - 1) / I.rows;
         I.tile0 = (int)b->tile_inst.size();
         for (int k = 0; k < I.tiles_x * I.tiles_y; ++k) b->tile_inst.push_back(i);
+        b->prefix[j] = (int)b->tile_inst.size();
+        ends[j] = I.end;
     }
     b->ntiles = (int)b->tile_inst.size();
     if (b->ntiles > b->max_tiles) return bfail(b, LBM_ACE_EINVAL, "work list larger than allocated");
     BK(b, cudaMemcpyAsync(b->d_inst, b->inst.data(), b->n * sizeof(BatchInst), cudaMemcpyHostToDevice, b->stream));
     BK(b, cudaMemcpyAsync(b->d_tile_inst, b->tile_inst.data(), b->ntiles * sizeof(int), cudaMemcpyHostToDevice,
                           b->stream));
+    BK(b, cudaMemcpyAsync(b->d_end_sorted, ends.data(), b->n * sizeof(long long), cudaMemcpyHostToDevice, b->stream));
+    BK(b, cudaMemcpyAsync(b->d_prefix, b->prefix.data(), b->n * sizeof(int), cudaMemcpyHostToDevice, b->stream));
     BK(b, cudaStreamSynchronize(b->stream));
     drop_graph(b);
     return LBM_ACE_OK;
@@ -200,33 +249,65 @@ void launch_batch_step(lbm_ace_batch* b)
 {
     if (b->model == LBM_ACE_MODEL_MODIFIED)
         ace_batch_step<MODEL_MODIFIED><<<b->grid, PAIR_THREADS, 0, b->stream>>>(b->d_inst, b->phase, b->d_tile_inst,
-                                                                              b->ntiles, b->ctl);
+                                                                              b->ctl);
     else
         ace_batch_step<MODEL_CONSERVATIVE><<<b->grid, PAIR_THREADS, 0, b->stream>>>(b->d_inst, b->phase, b->d_tile_inst,
-                                                                                  b->ntiles, b->ctl);
-    ace_batch_phase<<<(b->n + 255) / 256, 256, 0, b->stream>>>(b->ctl, b->d_inst, b->n, b->phase);
+                                                                                  b->ctl);
+    ace_batch_phase<<<(b->n + 255) / 256, 256, 0, b->stream>>>(b->ctl, b->d_inst, b->n, b->d_end_sorted, b->d_prefix,
+                                                              b->phase);
+    ace_batch_tick<<<1, 1, 0, b->stream>>>(b->ctl);
+}
+
+// The per-lattice baseline: one launch per lattice (all of its tiles, the batch's tile
+// heights), then the same phase and tick kernels. Lattices past their end launch
+// nothing but a no-op grid of their tiles, as a per-lattice scheduler would skip them
+// only on the host.
+void launch_per_lattice_step(lbm_ace_batch* b)
+{
+    for (int i = 0; i < b->n; ++i) {
+        const BatchInst& I = b->inst[i];
+        const int tiles = I.tiles_x * I.tiles_y;
+        if (b->model == LBM_ACE_MODEL_MODIFIED)
+            ace_batch_one<MODEL_MODIFIED><<<tiles, PAIR_THREADS, 0, b->stream>>>(b->d_inst, b->phase, i, b->ctl);
+        else
+            ace_batch_one<MODEL_CONSERVATIVE><<<tiles, PAIR_THREADS, 0, b->stream>>>(b->d_inst, b->phase, i, b->ctl);
+    }
+    ace_batch_phase<<<(b->n + 255) / 256, 256, 0, b->stream>>>(b->ctl, b->d_inst, b->n, b->d_end_sorted, b->d_prefix,
+                                                              b->phase);
     ace_batch_tick<<<1, 1, 0, b->stream>>>(b->ctl);
 }
 
 // Host-side reset of the device time and phases to the batch's time b->t.
+int active_tiles(const lbm_ace_batch* b, long long t)
+{
+    int a = 0;
+    for (int j = 0; j < b->n; ++j)
+        if (b->inst[b->order[j]].end > t) a = b->prefix[j];
+    return a;
+}
+
 int set_time(lbm_ace_batch* b)
 {
     std::vector<float2> ph(b->n);
     for (int i = 0; i < b->n; ++i)
         ph[i] = make_float2(float(std::cos(kPiB * (double)b->t / b->inst[i].T_period)),
                             float(std::cos(kPiB * ((double)b->t - 1.0) / b->inst[i].T_period)));
-    BatchCtl c{0, (int)b->t};
+    const int act = active_tiles(b, b->t);
+    BatchCtl c{0, (int)b->t, act, act};
     BK(b, cudaMemcpyAsync(b->ctl, &c, sizeof c, cudaMemcpyHostToDevice, b->stream));
     BK(b, cudaMemcpyAsync(b->phase, ph.data(), b->n * sizeof(float2), cudaMemcpyHostToDevice, b->stream));
     BK(b, cudaStreamSynchronize(b->stream));
     return LBM_ACE_OK;
 }
 
-int ensure_graph(lbm_ace_batch* b)
+int ensure_graph(lbm_ace_batch* b, bool per_lattice = false)
 {
-    if (b->exec) return LBM_ACE_OK;
+    if (b->exec && b->per_lattice_graph == per_lattice) return LBM_ACE_OK;
+    drop_graph(b);
+    b->per_lattice_graph = per_lattice;
     BK(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-    launch_batch_step(b);
+    if (per_lattice) launch_per_lattice_step(b);
+    else launch_batch_step(b);
     cudaGraph_t g = nullptr;
     BK(b, cudaStreamEndCapture(b->stream, &g));
     b->graph = g;
@@ -343,6 +424,8 @@ int lbm_ace_batch_init(const lbm_ace_params* params, int count, lbm_ace_batch** 
     BI(cudaMalloc(&b->d_tile_inst, (size_t)max_tiles * sizeof(int)));
     BI(cudaMalloc(&b->ctl, sizeof(BatchCtl)));
     BI(cudaMalloc(&b->phase, count * sizeof(float2)));
+    BI(cudaMalloc(&b->d_end_sorted, count * sizeof(long long)));
+    BI(cudaMalloc(&b->d_prefix, count * sizeof(int)));
     BI(cudaMalloc(&b->result, 2 * sizeof(double)));
     long long maxn = 0;
     for (const auto& q : b->p) maxn = std::max(maxn, (long long)q.nx * q.ny);
@@ -371,6 +454,7 @@ int lbm_ace_batch_init(const lbm_ace_params* params, int count, lbm_ace_batch** 
         I.delta = float(delta); I.inv1p2d = float(1.0 / (1.0 + 2.0 * delta));
         I.amp = float(q.vortex_sign * q.U0);
         I.T_period = q.T_period;
+        I.end = LLONG_MAX;
         I.mass_part = mp;
         mp += (size_t)((q.nx + PAIR_COLS - 1) / PAIR_COLS) * ((q.ny + kMinRows - 1) / kMinRows);
         // Eq. 14 tables, as in the single-lattice library
@@ -412,10 +496,6 @@ int lbm_ace_batch_init(const lbm_ace_params* params, int count, lbm_ace_batch** 
         BI(cudaGetLastError());
         BI(cudaStreamSynchronize(b->stream));
     }
-    {
-        const int rc0 = set_time(b);
-        if (rc0) return cleanup(rc0);
-    }
     int occ = 0;
     if (b->model == LBM_ACE_MODEL_MODIFIED)
         BI(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ace_batch_step<MODEL_MODIFIED>, PAIR_THREADS, 0));
@@ -444,8 +524,10 @@ int lbm_ace_batch_init(const lbm_ace_params* params, int count, lbm_ace_batch** 
         }
         BI(cudaMalloc(&b->seq_part, maxp * sizeof(double)));
     }
-    const int rc = build_tiles(b);
+    int rc = build_tiles(b);
+    if (rc == LBM_ACE_OK) rc = set_time(b);
     if (rc) return cleanup(rc);
+    b->grid_max = b->grid;
 #undef BI
     *out = b;
     return LBM_ACE_OK;
@@ -470,6 +552,7 @@ int lbm_ace_batch_step_sequential(lbm_ace_batch* b, long long n)
         const long long t = b->t + s;
         for (int i = 0; i < b->n; ++i) {
             const BatchInst& I = b->inst[i];
+            if (t >= I.end) continue; // retired
             StepArgs<float> a;
             a.fin = I.f[t & 1];
             a.fout = I.f[(t & 1) ^ 1];
@@ -516,6 +599,7 @@ int lbm_ace_batch_autotune(lbm_ace_batch* b, int steps_per_trial, int* rows_out)
     };
     auto trial = [&](float* ms) {
         int rc = build_tiles(b);
+        if (rc == LBM_ACE_OK) rc = set_time(b);
         if (rc) return rc;
         return time_steps(b, steps_per_trial, ms);
     };
@@ -537,6 +621,19 @@ int lbm_ace_batch_autotune(lbm_ace_batch* b, int steps_per_trial, int* rows_out)
             set_rows(nx, best_rows);
             if (rc) break;
         }
+        // CTAs per SM of the persistent grid, with the tile heights chosen so far
+        const int occ = std::max(1, b->grid_max / std::max(1, b->sms));
+        const int cur_grid = b->grid;
+        int best_grid = cur_grid;
+        for (int c = 1; c <= occ && rc == LBM_ACE_OK; ++c) {
+            const int gsz = c * b->sms;
+            if (gsz == cur_grid) continue;
+            b->grid = gsz;
+            float ms = 0.0f;
+            rc = trial(&ms);
+            if (rc == LBM_ACE_OK && ms < best) { best = ms; best_grid = gsz; }
+        }
+        b->grid = best_grid;
     }
     // restore the state and time, keep the chosen tiles
     cudaMemcpyAsync(b->pool, backup, b->pool_elems * sizeof(float), cudaMemcpyDeviceToDevice, b->stream);
@@ -546,9 +643,53 @@ int lbm_ace_batch_autotune(lbm_ace_batch* b, int steps_per_trial, int* rows_out)
     if (rc) return rc;
     if (rc_t) return rc_t;
     rc = build_tiles(b);
+    if (rc == LBM_ACE_OK) rc = set_time(b);
     if (rc) return rc;
     if (rows_out)
         for (int i = 0; i < b->n; ++i) rows_out[i] = b->inst[i].rows;
+    return LBM_ACE_OK;
+}
+
+int lbm_ace_batch_set_ends(lbm_ace_batch* b, const long long* end_steps)
+{
+    if (!b) return bfail(nullptr, LBM_ACE_EINVAL, "batch is NULL");
+    std::vector<long long> e(b->n);
+    for (int i = 0; i < b->n; ++i) {
+        long long v = end_steps ? end_steps[i] : (long long)std::llround(b->inst[i].T_period);
+        if (v < 0) v = LLONG_MAX;
+        if (v < b->t) return bfail(b, LBM_ACE_EINVAL, "lattice %d: end %lld is before the batch's time %lld", i, v, b->t);
+        e[i] = v;
+    }
+    BK(b, cudaStreamSynchronize(b->stream));
+    for (int i = 0; i < b->n; ++i) b->inst[i].end = e[i];
+    const int rc = build_tiles(b);
+    return rc ? rc : set_time(b);
+}
+
+long long lbm_ace_batch_lattice_steps(const lbm_ace_batch* b, int i)
+{
+    if (!b || i < 0 || i >= b->n) return -1;
+    return std::min(b->t, b->inst[i].end);
+}
+
+int lbm_ace_batch_active(const lbm_ace_batch* b, int* lattices, int* tiles)
+{
+    if (!b) return bfail(nullptr, LBM_ACE_EINVAL, "batch is NULL");
+    int n = 0;
+    for (int i = 0; i < b->n; ++i) n += b->inst[i].end > b->t;
+    if (lattices) *lattices = n;
+    if (tiles) *tiles = active_tiles(b, b->t);
+    return LBM_ACE_OK;
+}
+
+int lbm_ace_batch_step_per_lattice(lbm_ace_batch* b, long long n)
+{
+    if (!b) return bfail(nullptr, LBM_ACE_EINVAL, "batch is NULL");
+    if (n < 0) return bfail(b, LBM_ACE_EINVAL, "n must be >= 0");
+    int rc = ensure_graph(b, true);
+    if (rc) return rc;
+    for (long long s = 0; s < n; ++s) BK(b, cudaGraphLaunch(b->exec, b->stream));
+    b->t += n;
     return LBM_ACE_OK;
 }
 
@@ -562,7 +703,7 @@ int lbm_ace_batch_get_phi(lbm_ace_batch* b, int i, double* out, size_t count)
     rc = ensure_bscratch(b, n);
     if (rc) return rc;
     const int g = (int)std::min<long long>(((long long)n + 255) / 256, (long long)b->sms * 8);
-    ace_moment<float><<<g, 256, 0, b->stream>>>(I.f[b->t & 1], b->scratch, I.nx, I.ny);
+    ace_moment<float><<<g, 256, 0, b->stream>>>(I.f[std::min(b->t, I.end) & 1], b->scratch, I.nx, I.ny);
     BK(b, cudaGetLastError());
     BK(b, cudaMemcpyAsync(out, b->scratch, n * sizeof(double), cudaMemcpyDeviceToHost, b->stream));
     BK(b, cudaStreamSynchronize(b->stream));
@@ -576,8 +717,8 @@ int lbm_ace_batch_mass(lbm_ace_batch* b, int i, double* out)
     if (!out) return bfail(b, LBM_ACE_EINVAL, "out is NULL");
     const BatchInst& I = b->inst[i];
     const long long n9 = 9LL * I.nx * I.ny;
-    ace_sum_partials<float><<<b->n_red, RED_THREADS, 0, b->stream>>>(I.f[b->t & 1], n9, b->red_part);
-    ace_finalize<<<1, 32, 0, b->stream>>>(b->red_part, b->n_red, b->result);
+    ace_sum_partials_f32<<<b->n_red, RED_THREADS, 0, b->stream>>>(I.f[std::min(b->t, I.end) & 1], n9, b->red_part);
+    ace_finalize<<<1, RED_THREADS, 0, b->stream>>>(b->red_part, b->n_red, b->result);
     BK(b, cudaGetLastError());
     BK(b, cudaMemcpyAsync(out, b->result, sizeof(double), cudaMemcpyDeviceToHost, b->stream));
     BK(b, cudaStreamSynchronize(b->stream));
@@ -617,7 +758,7 @@ void lbm_ace_batch_destroy(lbm_ace_batch* b)
     if (b->stream) cudaStreamSynchronize(b->stream); else cudaDeviceSynchronize();
     drop_graph(b);
     void* bufs[] = {b->pool, b->tabs, b->mass_pool, b->seq_part, b->d_inst, b->d_tile_inst, b->ctl, b->phase,
-                    b->result, b->red_part, b->scratch};
+                    b->result, b->red_part, b->scratch, b->d_end_sorted, b->d_prefix};
     for (void* q : bufs) if (q) cudaFree(q);
     if (b->own_stream) cudaStreamDestroy(b->stream);
     delete b;

@@ -106,3 +106,87 @@ def test_full_batch_of_256_lattices_at_sampled_lattices():
                 assert np.abs(b.phi(i) - g.phi()).max() <= 1e-6
                 assert b.mass(i) == pytest.approx(g.mass(), rel=1e-6)
                 assert abs(b.mass(i) - m0) <= 1e-5 * m0
+
+
+def test_lattices_retire_at_their_own_end_step():
+    """Uneven runs: each lattice advances until its own end step and then keeps its
+    state, while the others go on; every lattice equals the same lattice run alone for
+    exactly its own number of steps."""
+    ends = [37, 60, 12, 60, 45]
+    specs = [dict(s, vortex_sign=-1.0) for s in SPECS]
+    with A.Batch(specs) as b:
+        b.set_ends(ends)
+        b.step(20)
+        assert b.active()[0] == sum(e > 20 for e in ends)
+        b.step(50)
+        assert b.t == 70 and b.active() == (0, 0)
+        for i, s in enumerate(SPECS):
+            assert b.lattice_steps(i) == ends[i]
+            ref, m0, m1 = standalone(s, ends[i])
+            assert np.abs(b.phi(i) - ref).max() <= 1e-6
+            assert b.mass(i) == pytest.approx(m1, rel=1e-6)
+
+
+def test_per_lattice_graph_and_host_launches_match_the_persistent_batch():
+    """The two baselines -- one launch per lattice per step, captured in a graph or issued
+    from the host -- give the batch's states, with retirement applied the same way."""
+    ends = [30, 18, 41, 25, 9]
+    specs = [dict(s, vortex_sign=-1.0) for s in SPECS]
+    with A.Batch(specs) as a, A.Batch(specs) as b, A.Batch(specs) as c:
+        for x in (a, b, c):
+            x.set_ends(ends)
+        a.step(45)
+        b.step_per_lattice(45)
+        c.step_sequential(45)
+        for i in range(len(SPECS)):
+            assert b.lattice_steps(i) == c.lattice_steps(i) == ends[i]
+            assert np.array_equal(a.phi(i), b.phi(i))
+            assert np.abs(a.phi(i) - c.phi(i)).max() <= 1e-6
+
+
+def test_default_ends_are_the_periods_and_the_shape_returns():
+    """set_ends() without a list ends each lattice at its period T (rounded), the time at
+    which the single-vortex benchmark compares the shape with the initial one; one
+    lattice is checked against the FP64 oracle at its T."""
+    specs = [dict(nx=64, ny=64, tau=0.8, eps=1.0, U0=0.04, T_period=T, xc=32.0, yc=44.0, R=9.6, vortex_sign=-1.0)
+             for T in (96.0, 140.4, 201.0)]
+    with A.Batch(specs) as b:
+        b.set_ends()
+        b.step(250)
+        assert [b.lattice_steps(i) for i in range(3)] == [96, 140, 201]
+        s = specs[1]
+        phi0 = W.disk_phi0(64, 64, s["xc"], s["yc"], s["R"], s["eps"])
+        p = O.Params(nx=64, ny=64, tau=s["tau"], eps=s["eps"], U0=s["U0"], T=s["T_period"], sign=-1.0)
+        ref = O.Sim(p, phi0).step(140).phi()
+        assert np.abs(b.phi(1) - ref).max() <= 2e-5
+        for i, sp in enumerate(specs):
+            e2 = np.sqrt(((b.phi(i) - phi0) ** 2).sum() / (phi0 ** 2).sum())
+            assert e2 < 0.05  # the disk is back near its start at t = T
+
+
+def test_set_ends_rejects_an_end_in_the_past():
+    with A.Batch([dict(s, vortex_sign=-1.0) for s in SPECS[:2]]) as b:
+        b.step(10)
+        with pytest.raises(A.LbmAceError) as e:
+            b.set_ends([5, 20])
+        assert e.value.status == A.EINVAL
+        b.set_ends([10, -1])
+        b.step(5)
+        assert b.lattice_steps(0) == 10 and b.lattice_steps(1) == 15
+
+
+def test_autotune_sweeps_the_persistent_grid():
+    """The autotuner also picks the persistent grid: a whole number of CTAs per SM, at
+    most the occupancy limit the batch starts with; the state is unaffected."""
+    torch = pytest.importorskip("torch")
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    specs = [dict(s, vortex_sign=-1.0) for s in SPECS]
+    with A.Batch(specs) as b:
+        g0 = b.info()["grid"]
+        b.autotune(steps_per_trial=2)
+        g = b.info()["grid"]
+        assert g % sms == 0 and sms <= g <= g0
+        b.step(12)
+        for i, s in enumerate(SPECS):
+            ref, _, _ = standalone(s, 12)
+            assert np.abs(b.phi(i) - ref).max() <= 1e-6
