@@ -95,6 +95,15 @@ int lbm_ace_net_metrics(lbm_ace_net* net, const float* phi, int ny, int nx, doub
 /* Block until the net's device work has finished. */
 int lbm_ace_net_synchronize(lbm_ace_net* net);
 
+/* Failure self-test of the tensor-core kernels' bounded waits (a service of this
+ * library; the paper has no counterpart). One thread waits, with the same bounded
+ * mbarrier wait those kernels use, on a barrier that nothing arrives on, gives up after
+ * limit_cycles SM clock cycles (1 .. 2e9, the kernels' own limit) and raises the net's
+ * error flag as they would; no tensor-core operation runs and no tensor memory is held.
+ * Synchronous. Returns LBM_ACE_ETIMEOUT, the expected result, and clears the flag: the
+ * net then works as before. LBM_ACE_EINVAL for a limit out of range. */
+int lbm_ace_net_wait_selftest(lbm_ace_net* net, long long limit_cycles);
+
 /* Launch shape of the persistent tensor-core kernels: CTAs launched (at most) for the
  * hidden layers and for layer 5, the resident CTAs per SM the occupancy calculator
  * reports for each, and the SM count. Any pointer may be NULL. */

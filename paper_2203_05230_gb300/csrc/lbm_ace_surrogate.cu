@@ -337,10 +337,12 @@ __device__ __forceinline__ void umma_commit(unsigned mbar)
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
 
-// Wait for the phase `parity` of an mbarrier, giving up after ~1 s of SM clock. Each
-// try_wait may suspend the warp for up to 0.1 ms (a hint to the hardware), so a waiting
-// warp does not spin on the issue slots.
-__device__ __forceinline__ bool mbar_wait(unsigned mbar, unsigned parity)
+constexpr long long kSurrWaitCycles = 2000000000LL; // ~1 s of SM clock
+
+// Wait for the phase `parity` of an mbarrier, giving up after `limit` cycles of SM clock
+// (~1 s for the kernels). Each try_wait may suspend the warp for up to 0.1 ms (a hint to
+// the hardware), so a waiting warp does not spin on the issue slots.
+__device__ __forceinline__ bool mbar_wait_limit(unsigned mbar, unsigned parity, long long limit)
 {
     const long long t0 = clock64();
     for (;;) {
@@ -348,8 +350,13 @@ __device__ __forceinline__ bool mbar_wait(unsigned mbar, unsigned parity)
         asm volatile("{\n.reg .pred q;\nmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2, %3;\nselp.u32 %0, 1, 0, q;\n}\n"
                      : "=r"(done) : "r"(mbar), "r"(parity), "r"(100000u) : "memory");
         if (done) return true;
-        if (clock64() - t0 > 2000000000LL) return false;
+        if (clock64() - t0 > limit) return false;
     }
+}
+
+__device__ __forceinline__ bool mbar_wait(unsigned mbar, unsigned parity)
+{
+    return mbar_wait_limit(mbar, parity, kSurrWaitCycles);
 }
 
 #define TMEM_LD_OUT16(r) "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), \
@@ -433,6 +440,19 @@ constexpr int umma_smem_bytes() { return 9 * 4 * N * 16 + 2 * u_halo<R>(); }
 __device__ __forceinline__ void mbar_init(unsigned mbar, unsigned count)
 {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(mbar), "r"(count));
+}
+
+// Failure self-test: one thread initialises an mbarrier that nothing ever arrives on
+// and waits for it with the tensor-core kernels' own bounded wait, here with a short
+// limit; when the wait gives up it raises the network's error flag the way those
+// kernels do. No tensor-core operation is issued and no tensor memory is allocated.
+__global__ void surr_wait_selftest(long long limit, int* err)
+{
+    __shared__ __align__(8) unsigned long long bar;
+    const unsigned mbar = (unsigned)__cvta_generic_to_shared(&bar);
+    mbar_init(mbar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    if (!mbar_wait_limit(mbar, 0, limit)) atomicExch(err, 1);
 }
 __device__ __forceinline__ void mbar_arrive(unsigned mbar)
 {
@@ -1597,6 +1617,18 @@ int lbm_ace_net_synchronize(lbm_ace_net* n)
 {
     if (!n) return nfail(nullptr, LBM_ACE_EINVAL, "net is NULL");
     NetDevice gd(n->dev);
+    NCK(n, cudaStreamSynchronize(n->stream));
+    return check_err(n);
+}
+
+int lbm_ace_net_wait_selftest(lbm_ace_net* n, long long limit_cycles)
+{
+    if (!n) return nfail(nullptr, LBM_ACE_EINVAL, "net is NULL");
+    if (limit_cycles < 1 || limit_cycles > kSurrWaitCycles)
+        return nfail(n, LBM_ACE_EINVAL, "limit_cycles = %lld: must be in [1, %lld]", limit_cycles, kSurrWaitCycles);
+    NetDevice gd(n->dev);
+    surr_wait_selftest<<<1, 1, 0, n->stream>>>(limit_cycles, n->derr);
+    NCK(n, cudaGetLastError());
     NCK(n, cudaStreamSynchronize(n->stream));
     return check_err(n);
 }
