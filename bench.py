@@ -40,7 +40,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "MLUPS"
 KERNEL_NAME = {1: "ace_step", 2: "ace_step_bulk", 3: "ace_step_warp", 4: "ace_step_pair", 5: "ace_step_dev",
-               6: "ace_step_tb2"}
+               6: "ace_step_tb2", 7: "ace_step_dev4", 8: "ace_step_quad"}
 STEPS_PER_LAUNCH = {6: 2}   # the two-step kernel: one launch advances two steps
 BYTES_PER_LUP = {"f64": 160, "f32": 80, "f16dev": 44, "bf16dev": 44}
 L2_NOTE = "inputs larger than L2: 2 x 151 MB FP32 population buffers + 16.8 MB phi plane"
@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--precision", default="f32", choices=["f32", "f64", "f16dev", "bf16dev"])
     ap.add_argument("--rows", type=int, default=0, help="rows per CTA (0: library default)")
     ap.add_argument("--variant", type=int, default=0, help="step kernel: 0 auto, 1 direct loads, 2 bulk-copy pipeline, 3 independent warps, 4 column pairs, "
-                    "6 two steps per launch")
+                    "6 two steps per launch; 16-bit storage: 5 column pairs, 7 column quads")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -65,6 +65,10 @@ def parse():
     ap.add_argument("--surr-traj", type=int, default=625,
                     help="training trajectories of 32 windows (surrogate mode; 0: forward timing only)")
     ap.add_argument("--surr-train-steps", type=int, default=20000)
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the record of the 16-bit, batched and surrogate forms against plain FP32")
+    ap.add_argument("--forms-train-steps", type=int, default=20000,
+                    help="Adam steps of the surrogate trained inside the forms record")
     return ap.parse_args()
 
 
@@ -339,7 +343,9 @@ def run_ours(args):
                                                     3: "ace_step_warp (independent warps)",
                                                     4: "ace_step_pair (two columns per thread)",
                                                     5: "ace_step_dev (16-bit deviations)",
-                                                    6: "ace_step_tb2 (two steps per launch)"}[shape[4]],
+                                                    6: "ace_step_tb2 (two steps per launch)",
+                                                    7: "ace_step_dev4 (16-bit deviations, four columns per thread)",
+                                                    8: "ace_step_quad (four columns per thread, warp strips)"}[shape[4]],
                                          "steps_per_launch": spl},
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -355,11 +361,63 @@ def run_ours(args):
         line["clock_note"] = note
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, v, args.cpu_seconds)
+    if ws == 1 and not args.no_forms and args.precision == "f32" and args.L == 2048:
+        line["forms"] = forms_record(args, stream)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def forms_record(args, stream):
+    """The three extra forms against plain FP32 on the same GPU, in this process:
+    16-bit deviation storage on the 4096^2 precision workload (speed by CUDA events and
+    errors over its full period T = 16384 against FP64 and FP32 runs), the 256-lattice
+    batch run to each lattice's own period (aggregate MLUPS by CUDA events; speedups
+    over one launch per lattice per step, graph-captured and host-issued), and the
+    learned surrogate (trained here for --forms-train-steps Adam steps; one 256^2
+    vortex period by the hybrid against the fastest plain FP32 form of that lattice)."""
+    import torch
+    from paper_2203_05230_gb300 import experiments as E
+    from paper_2203_05230_gb300 import lbm_ace as A
+    from paper_2203_05230_gb300 import surrogate as SG
+    from paper_2203_05230_gb300 import workloads as W
+    rec = {}
+    t0 = time.perf_counter()
+    rec["storage_16bit"] = E.storage_forms(L=4096, T=16384, stream=stream)
+    rec["storage_16bit"]["record_seconds"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    rec["batch"] = E.batch_uneven(256, stream=stream)
+    rec["batch"]["record_seconds"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    L = W.SURROGATE_TILE
+    data = SG.generate(625, 32, L=L, seed=0, stream=stream)
+    n_train = (625 - 25) * 32
+    sur = {}
+    with A.Net(0, stream) as net:
+        net.set_params(W.surrogate_init_params(seed=0))
+        tr = SG.Trainer(net, data, batch=16, seed=0)
+        t1 = time.perf_counter()
+        tr.train(args.forms_train_steps, train_pairs=np.arange(n_train))
+        sur["training"] = {"pairs": data.n_pairs, "held_out_pairs": data.n_pairs - n_train,
+                           "adam_steps": args.forms_train_steps, "seconds": time.perf_counter() - t1,
+                           **{k: v for k, v in tr.evaluate(np.arange(n_train, data.n_pairs)).items()}}
+        del data
+        ro = SG.vortex_rollout(net, L=L, stream=stream)
+    plain = E.plain_fp32_fastest(L=L)
+    best = plain["fastest"]
+    sur["plain_fp32"] = plain
+    sur["hybrid"] = {k: ro[k] for k in ("hybrid_seconds", "E2_vs_lbm_T", "E2_vs_lbm_half", "E2_lbm_shape_return",
+                                        "E2_hybrid_shape_return", "mass_drift_hybrid", "surrogate_windows",
+                                        "fallback_windows", "max_width_dev")}
+    sur["hybrid"]["mlups_equivalent"] = L * L * ro["T"] / ro["hybrid_seconds"] / 1e6
+    sur["speedup_vs_fastest_plain_fp32"] = plain["seconds"][best] / ro["hybrid_seconds"]
+    sur["speedup_vs_plain_fp32_launches"] = plain["seconds"]["launches"] / ro["hybrid_seconds"]
+    sur["phi_l2_vs_plain_fp32_at_T"] = ro["E2_vs_lbm_T"]
+    sur["record_seconds"] = time.perf_counter() - t0
+    rec["surrogate"] = sur
+    return rec
 
 
 def run_e2e(args, v, prec, stream, dev, A, ws=1):

@@ -129,6 +129,155 @@ def precision_study(L=4096, T=16384, eps=1.0):
                      "the FP64 GPU run", "forms": out}
 
 
+def _events_seconds(fn, stream):
+    """Run fn() between two CUDA events on `stream` (synchronised on both sides)."""
+    import torch
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3
+
+
+def storage_forms(L=4096, T=16384, eps=1.0, speed_steps=300, accuracy=True, stream=None):
+    """The 16-bit deviation forms against plain FP32 on the same lattice (the precision
+    workload: single vortex, eps 1, tau 0.8, U0 0.04, period T): speed by CUDA events over
+    `speed_steps` steps after a warm-up, each form in its own lattice on `stream`; with
+    `accuracy`, one full period of FP64, FP32, FP16 and BF16 storage and the errors at T
+    (phi-L2 against the FP64 and the FP32 runs, mass drift, interface width)."""
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    v = W.Vortex(L=L, eps=eps, T=T)
+    kw = dict(nx=L, ny=L, tau=v.tau, eps=eps, U0=v.U0, T_period=float(T), vortex_sign=v.sign, phi0=v.phi0(),
+              stream=s.cuda_stream)
+    out = {"workload": f"single vortex {L}x{L}, eps {eps}, tau {v.tau}, U0 {v.U0}, T {T}", "speed": {}}
+    for name, prec in (("f32", A.F32), ("f16dev", A.F16DEV), ("bf16dev", A.BF16DEV)):
+        with A.Lattice(precision=prec, **kw) as g:
+            g.step(20)
+            sec = _events_seconds(lambda: g.step(speed_steps), s)
+            shape = g.launch_shape()
+        out["speed"][name] = {"mlups": L * L * speed_steps / sec / 1e6, "us_per_step": sec / speed_steps * 1e6,
+                              "bytes_per_lup": 80 if prec == A.F32 else 44, "kernel_variant": shape[4],
+                              "rows_per_cta": shape[1]}
+    f32 = out["speed"]["f32"]["mlups"]
+    for name in ("f16dev", "bf16dev"):
+        out["speed"][name]["speedup_vs_f32"] = out["speed"][name]["mlups"] / f32
+    if accuracy:
+        res, phi = {}, {}
+        phi0 = v.phi0()
+        for name, prec in (("f64", A.F64), ("f32", A.F32), ("f16dev", A.F16DEV), ("bf16dev", A.BF16DEV)):
+            with A.Lattice(precision=prec, **kw) as g:
+                m0 = g.mass()
+                sec = _events_seconds(lambda: g.step(T), s)
+                phi[name] = g.phi()
+                res[name] = {"mass_drift": (g.mass() - m0) / m0, "width_T": interface_width(phi[name]),
+                             "period_seconds": sec}
+        for name in res:
+            res[name]["phi_l2_vs_f64"] = errors(phi[name], phi["f64"])["E2"]
+            res[name]["phi_l2_vs_f32"] = errors(phi[name], phi["f32"])["E2"]
+            res[name]["shape_return_phi_l2"] = errors(phi[name], phi0)["E2"]
+        out["accuracy_at_T"] = res
+        out["width_t0"] = interface_width(phi0)
+    return out
+
+
+def batch_uneven(count=256, seed=0, window=200, seq_window=20, tune_steps=2, stream=None, check=8):
+    """The batched workload run to each lattice's own period: autotuned, one persistent
+    graph-replayed launch per step, lattices retiring at t = T_i; aggregate MLUPS by CUDA
+    events over the whole run. Then, with the ends lifted, the same `window` steps of all
+    lattices as the persistent batch, as one launch per lattice per step captured in a
+    graph, and (`seq_window` steps) as host-issued launches in the single-lattice
+    library's launch shape. `check` lattices are compared at their T_i with the same
+    lattice run alone (phi-L2) and with their initial field (shape return)."""
+    import torch
+    # a stream of its own: a batch given the legacy default stream would make one
+    # itself, and events on the default stream would not bracket its work
+    s = stream if stream is not None and stream.cuda_stream != 0 else torch.cuda.Stream()
+    specs = batch_specs(count, seed)
+    ends = [int(round(sp["T_period"])) for sp in specs]
+    nodes = [sp["nx"] * sp["ny"] for sp in specs]
+    out = {"workload": f"{count} single-vortex lattices, sides {sorted({sp['nx'] for sp in specs})}, FP32, "
+                       f"each to its own period T_i in [8 L, 16 L]",
+           "nodes": int(sum(nodes)), "lattice_updates": int(sum(n * e for n, e in zip(nodes, ends))),
+           "max_T": max(ends)}
+    rng = np.random.default_rng(seed + 1)
+    picks = sorted({int(np.argmin(nodes)), int(np.argmax(nodes)),
+                    *[int(i) for i in rng.choice(count, max(0, check - 2), replace=False)]})
+    with A.Batch(specs, stream=s) as b:
+        t0 = time.perf_counter()
+        b.autotune(steps_per_trial=tune_steps)
+        out["autotune_seconds"] = time.perf_counter() - t0
+        out["grid"] = b.info()["grid"]
+        b.set_ends()
+        sec = _events_seconds(lambda: b.step(max(ends)), s)
+        out["run_seconds"] = sec
+        out["mlups_uneven_run"] = out["lattice_updates"] / sec / 1e6
+        assert all(b.lattice_steps(i) == ends[i] for i in range(count))
+        checks = []
+        for i in picks:
+            sp = specs[i]
+            phi_b = b.phi(i)
+            with A.Lattice(precision=A.F32, velocity_kind=A.VEL_SINGLE_VORTEX, stream=s.cuda_stream, **sp) as g:
+                phi0 = g.phi()
+                g.step(ends[i])
+                ref = g.phi()
+            checks.append({"lattice": i, "L": sp["nx"], "T": ends[i], "phi_l2_vs_alone": errors(phi_b, ref)["E2"],
+                           "shape_return_phi_l2": errors(phi_b, phi0)["E2"]})
+        out["checked_lattices"] = checks
+        b.set_ends([-1] * count)
+        sec_p = _events_seconds(lambda: b.step(window), s)
+        sec_g = _events_seconds(lambda: b.step_per_lattice(window), s)
+        sec_h = _events_seconds(lambda: b.step_sequential(seq_window), s)
+    n = out["nodes"]
+    out["window"] = {"steps": window, "mlups_persistent": n * window / sec_p / 1e6,
+                     "mlups_per_lattice_graph": n * window / sec_g / 1e6,
+                     "mlups_host_launches": n * seq_window / sec_h / 1e6, "host_launch_steps": seq_window}
+    out["speedup_vs_per_lattice_graph"] = out["window"]["mlups_persistent"] / out["window"]["mlups_per_lattice_graph"]
+    out["speedup_vs_host_launches"] = out["window"]["mlups_persistent"] / out["window"]["mlups_host_launches"]
+    return out
+
+
+def plain_fp32_fastest(L=256, eps=1.0, tau=0.8, U0=0.04, T=None, stream=None):
+    """One period of the plain FP32 lattice on L x L in four launch forms, timed by CUDA
+    events: per-step launches (programmatic dependent launch), the whole period captured
+    in one CUDA graph, a persistent batch of one lattice (graph replays), and the
+    two-steps-per-launch kernel. Returns the seconds of each and the fastest."""
+    import torch
+    s = torch.cuda.Stream()
+    T = int(T if T else 16 * L)
+    v = W.Vortex(L=L, eps=eps, tau=tau, U0=U0, T=T)
+    kw = dict(nx=L, ny=L, tau=tau, eps=eps, U0=U0, T_period=float(T), vortex_sign=v.sign, phi0=v.phi0(),
+              precision=A.F32, stream=s.cuda_stream)
+    res = {}
+    with torch.cuda.stream(s):
+        with A.Lattice(**kw) as g:
+            g.step(8)
+            res["launches"] = _events_seconds(lambda: g.step(T), s)
+        with A.Lattice(**kw) as g:
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph, stream=s):
+                g.step(T)
+            res["graph"] = _events_seconds(graph.replay, s)
+            phi_graph = g.phi()
+        with A.Lattice(**kw) as g:
+            g.step(T)
+            assert np.array_equal(g.phi(), phi_graph)  # the captured period is the same run
+        spec = {k: kw[k] for k in ("nx", "ny", "tau", "eps", "U0", "T_period", "vortex_sign")}
+        spec.update(xc=v.xc, yc=v.yc, R=v.R)
+        with A.Batch([spec], stream=s) as b:
+            b.autotune(steps_per_trial=8)
+            b.step(8)
+            res["batch_of_one"] = _events_seconds(lambda: b.step(T), s)
+        with A.Lattice(kernel_variant=A.KERNEL_TWO_STEP, **kw) as g:
+            g.step(8)
+            res["two_steps_per_launch"] = _events_seconds(lambda: g.step(T), s)
+    best = min(res, key=res.get)
+    return {"L": L, "T": T, "seconds": res, "mlups": {k: L * L * T / x / 1e6 for k, x in res.items()},
+            "fastest": best}
+
+
 def batch_specs(count=256, seed=0):
     """The batched workload: `count` single-vortex lattices with seeded draws (sides
     from {128, ..., 1024}, centre in [0.3, 0.7] L, radius in [0.1, 0.2] L, eps in
