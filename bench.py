@@ -176,10 +176,10 @@ def rejected(clk):
 
 
 def kernel_source_hash() -> str:
-    """Hash of the step kernels' device sources (both variants)."""
+    """Hash of the step kernels' device sources (all variants)."""
     h = hashlib.sha256()
     for name in ("ace_kernels.cuh", "ace_step_bulk.cuh", "ace_step_warp.cuh", "ace_step_pair.cuh",
-                 "ace_step_dev.cuh"):
+                 "ace_step_dev.cuh", "ace_step_dev4.cuh", "ace_step_quad.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2203_05230_gb300", "csrc", name), "rb").read())
     return h.hexdigest()[:16]
 

@@ -648,41 +648,12 @@ __device__ __forceinline__ void block_sum_to(double v, double* sh, double* part)
     if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
 }
 
-// Partial sums of n FP32 values (16-byte aligned) for the global mass: 16-byte loads,
-// MassAcc4 per thread over a fixed strided subset of the groups of four, the n % 4 last
-// values in FP64 by the first threads of CTA 0, then a fixed tree per CTA.
-// Deterministic, bound by HBM bandwidth rather than by the FP64 pipe.
-static __global__ void __launch_bounds__(RED_THREADS) ace_sum_partials_f32(const float* __restrict__ v, long long n,
-                                                                           double* __restrict__ part)
+// Fixed-order compensated sum of part[0 .. n) by the CTA's RED_THREADS threads: each a
+// Neumaier sum over a strided subset, then a pairwise tree whose nodes add two
+// (sum, compensation) pairs with an error-free two-sum of the sums. Returns the total
+// in thread 0.
+__device__ __forceinline__ double block_final_sum(const double* part, int n, double* ss, double* sc)
 {
-    __shared__ double sh[RED_THREADS];
-    const float4* v4 = reinterpret_cast<const float4*>(v);
-    const long long n4 = n >> 2;
-    const long long stride = (long long)gridDim.x * RED_THREADS;
-    MassAcc4 acc;
-    long long k = blockIdx.x * (long long)RED_THREADS + threadIdx.x;
-    for (; k + 3 * stride < n4; k += 4 * stride) { // four independent 16-byte loads in flight
-        const float4 q0 = v4[k], q1 = v4[k + stride], q2 = v4[k + 2 * stride], q3 = v4[k + 3 * stride];
-        acc.add(q0);
-        acc.add(q1);
-        acc.add(q2);
-        acc.add(q3);
-    }
-    for (; k < n4; k += stride) acc.add(v4[k]);
-    double s = acc.total();
-    if (blockIdx.x == 0 && threadIdx.x < (n & 3)) s += (double)v[4 * n4 + threadIdx.x];
-    block_sum_to(s, sh, part);
-}
-
-// Final sum of n partials by one CTA of RED_THREADS threads: each thread a compensated
-// sum over a fixed strided subset, then a fixed pairwise tree in shared memory whose
-// nodes add two (sum, compensation) pairs with an error-free two-sum of the sums. Fixed
-// order, so deterministic; every level runs in parallel (a single warp summing a few
-// thousand partials one after another spent tens of microseconds in FP64 latencies).
-static __global__ void __launch_bounds__(RED_THREADS) ace_finalize(const double* __restrict__ part, int n,
-                                                                   double* __restrict__ out)
-{
-    __shared__ double ss[RED_THREADS], sc[RED_THREADS];
     double s = 0.0, c = 0.0;
     for (int k = threadIdx.x; k < n; k += RED_THREADS) neumaier(s, c, part[k]);
     ss[threadIdx.x] = s;
@@ -699,7 +670,67 @@ static __global__ void __launch_bounds__(RED_THREADS) ace_finalize(const double*
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0) out[0] = ss[0] + sc[0];
+    return ss[0] + sc[0];
+}
+
+// After every CTA has written its partial: the CTA that finishes last (a ticket counter
+// in global memory, zero between calls) sums all partials in their fixed order into
+// *out and resets the counter. Saves the separate finishing launch; the result does not
+// depend on which CTA finishes last.
+__device__ __forceinline__ void finish_in_last_block(const double* part, unsigned* done, double* out, double* ss,
+                                                     double* sc)
+{
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        __threadfence(); // this CTA's partial is visible before its ticket
+        last = atomicAdd(done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const double total = block_final_sum(part, gridDim.x, ss, sc);
+    if (threadIdx.x == 0) {
+        out[0] = total;
+        *done = 0u;
+    }
+}
+
+// Partial sums of n FP32 values (16-byte aligned) for the global mass: 16-byte loads,
+// MassAcc4 per thread over a fixed strided subset of the groups of four, the n % 4 last
+// values in FP64 by the first threads of CTA 0, then a fixed tree per CTA.
+// Deterministic, bound by HBM bandwidth rather than by the FP64 pipe.
+static __global__ void __launch_bounds__(RED_THREADS) ace_sum_partials_f32(const float* __restrict__ v, long long n,
+                                                                           double* __restrict__ part,
+                                                                           unsigned* done, double* out)
+{
+    __shared__ double sh[RED_THREADS], sc[RED_THREADS];
+    const float4* v4 = reinterpret_cast<const float4*>(v);
+    const long long n4 = n >> 2;
+    const long long stride = (long long)gridDim.x * RED_THREADS;
+    MassAcc4 acc;
+    long long k = blockIdx.x * (long long)RED_THREADS + threadIdx.x;
+    for (; k + 3 * stride < n4; k += 4 * stride) { // four independent 16-byte loads in flight
+        const float4 q0 = v4[k], q1 = v4[k + stride], q2 = v4[k + 2 * stride], q3 = v4[k + 3 * stride];
+        acc.add(q0);
+        acc.add(q1);
+        acc.add(q2);
+        acc.add(q3);
+    }
+    for (; k < n4; k += stride) acc.add(v4[k]);
+    double s = acc.total();
+    if (blockIdx.x == 0 && threadIdx.x < (n & 3)) s += (double)v[4 * n4 + threadIdx.x];
+    block_sum_to(s, sh, part);
+    finish_in_last_block(part, done, out, sh, sc);
+}
+
+// Final sum of n partials by one CTA (block_final_sum), for partials written by kernels
+// that do not finish their own sums.
+static __global__ void __launch_bounds__(RED_THREADS) ace_finalize(const double* __restrict__ part, int n,
+                                                                   double* __restrict__ out)
+{
+    __shared__ double ss[RED_THREADS], sc[RED_THREADS];
+    const double total = block_final_sum(part, n, ss, sc);
+    if (threadIdx.x == 0) out[0] = total;
 }
 
 } // namespace lbmace

@@ -377,10 +377,11 @@ __global__ void ace_push_state_dev(const double* __restrict__ f, const double* _
 template <typename S>
 __global__ void __launch_bounds__(RED_THREADS) ace_sum_partials_dev(const unsigned short* __restrict__ g,
                                                                     const float* __restrict__ phi, long long n,
-                                                                    double* __restrict__ part)
+                                                                    double* __restrict__ part, unsigned* done,
+                                                                    double* out)
 {
     using C = Dev16<S>;
-    __shared__ double sh[RED_THREADS];
+    __shared__ double sh[RED_THREADS], sc[RED_THREADS];
     const long long n16 = 9 * n;
     const uint2* g4 = reinterpret_cast<const uint2*>(g);
     const float4* p4 = reinterpret_cast<const float4*>(phi);
@@ -398,6 +399,7 @@ __global__ void __launch_bounds__(RED_THREADS) ace_sum_partials_dev(const unsign
         if (threadIdx.x < (n & 3)) s += (double)phi[4 * (n >> 2) + threadIdx.x];
     }
     block_sum_to(s, sh, part);
+    finish_in_last_block(part, done, out, sh, sc);
 }
 
 } // namespace lbmace

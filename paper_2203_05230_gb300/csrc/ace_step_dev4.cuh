@@ -17,9 +17,12 @@
 //     warp never waits for the slowest warp of its CTA.
 //   * The pulled populations of the row that collides next are parked in shared memory
 //     (9 x 16 bytes per thread, two row buffers) instead of registers.
-//   * 3 CTAs of 128 threads per SM: up to 168 registers per thread, no spills. (At 4 CTAs
-//     the 128-register cap spilled and ran slower; at 2 the SM lacks warps to hide
-//     latency.)
+//   * 3 or 4 CTAs of 128 threads per SM (the template parameter MINB, chosen by the host
+//     from the lattice size): at 3, up to 168 registers and no spills; at 4, a
+//     128-register cap (a 4-byte spill) and a third more warps to hide latency, which
+//     pays on large lattices (4096^2: 105.6k against 101.5k MLUPS) and not on small ones,
+//     where the shorter row bands of the one-wave launch cost more (2048^2: 92.1k against
+//     95.1k). At 2 CTAs the SM lacks warps.
 //   * The row loop is not unrolled: an unrolled body (to rotate the rolling window of
 //     phi(t-1) rows without register moves) overflowed the instruction cache, which cost
 //     far more than the moves.
@@ -38,23 +41,6 @@ constexpr int QUAD_THREADS = 128;
 constexpr int QUAD_COLS = 4 * QUAD_THREADS; // columns of a CTA
 constexpr int QUAD_STRIP = 128;             // columns of one warp
 constexpr int QUAD_WARPS = QUAD_THREADS / 32;
-constexpr int QUAD_MIN_CTAS = 3;
-#ifndef DEV4_L2PF
-#define DEV4_L2PF 0 // experiment: rows ahead of the loads that lane 0 of each warp prefetches into L2
-#endif
-
-// Prefetch bytes [lo, hi) of a buffer into L2 (bulk prefetch: 16-byte aligned start,
-// length a multiple of 16; the range is rounded inwards at the buffer's end).
-__device__ __forceinline__ void l2_prefetch(const void* base, size_t lo, size_t hi, size_t end)
-{
-    lo &= ~(size_t)15;
-    hi = (hi + 15) & ~(size_t)15;
-    if (hi > (end & ~(size_t)15)) hi = end & ~(size_t)15;
-    if (hi > lo)
-        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"((const char*)base + lo), "r"((unsigned)(hi - lo))
-                     : "memory");
-}
-
 struct QuadSmem {
     float chi[QUAD_WARPS][4][QUAD_STRIP + 8]; // psi ring per warp: index j holds column x0 + j - 4
     float4 park[2][9][QUAD_THREADS];         // pulled f of one row: [buffer][plane][thread] (nodes 0..3)
@@ -161,20 +147,6 @@ __device__ __forceinline__ void dev4_tile(const DevArgs<S>& d, const StepArgs<fl
         }
         const int yc = UP ? y1 - k + 1 : y0 + k - 2;
         if (yc >= y0 && yc < y1) vr_next = vel.rowv(cq[0], xq, yc);
-#if DEV4_L2PF
-        if (lane == 0 && k + DEV4_L2PF < nk) { // the rows the loads DEV4_L2PF iterations ahead read
-            const int q = wrap_idx(UP ? y1 - k - DEV4_L2PF : y0 - 1 + k + DEV4_L2PF, a.ny);
-            const int qm = q == 0 ? a.ny - 1 : q - 1, qp = q == a.ny - 1 ? 0 : q + 1;
-            const size_t gend = (size_t)9 * plane * 2, xb0 = (size_t)(x0 > 0 ? x0 - 8 : 0), xb1 = (size_t)(x0 + w + 8);
-            for (int i = 0; i < 9; ++i) {
-                const int rr = cy_of(i) > 0 ? qm : (cy_of(i) < 0 ? qp : q);
-                const size_t row0 = ((size_t)i * plane + (size_t)rr * nxu) * 2;
-                l2_prefetch(d.gin, row0 + 2 * xb0, row0 + 2 * min(xb1, (size_t)nxu), gend);
-            }
-            const size_t prow = (size_t)(UP ? qm : qp) * nxu * 4;
-            l2_prefetch(d.phin, prow + 4 * xb0, prow + 4 * min(xb1, (size_t)nxu), (size_t)plane * 4);
-        }
-#endif
     };
 
     // phi(t-1) window of iteration k: rows r(k - 1) (Wb), r(k) (Wc), r(k + 1) (Wa)
@@ -343,8 +315,8 @@ __device__ __forceinline__ void dev4_tile(const DevArgs<S>& d, const StepArgs<fl
     }
 }
 
-template <typename S, int MODEL, class Vel>
-__global__ void __launch_bounds__(QUAD_THREADS, QUAD_MIN_CTAS)
+template <typename S, int MODEL, class Vel, int MINB>
+__global__ void __launch_bounds__(QUAD_THREADS, MINB)
 ace_step_dev4(const DevArgs<S> d, const StepArgs<float> a, const Vel vel)
 {
     extern __shared__ __align__(16) unsigned char dev4_smem[];

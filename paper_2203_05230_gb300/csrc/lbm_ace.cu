@@ -31,6 +31,10 @@ namespace {
 thread_local std::string g_err; // errors raised before a context exists
 
 constexpr double kPi = 3.14159265358979323846;
+// phi0 fields up to this many values are checked for non-finite entries on the host
+// before any device work; larger ones right after their upload, on the device (a host
+// pass over a 2048^2 field costs milliseconds)
+constexpr size_t kHostCheckMax = 1u << 16;
 
 struct VelState {
     // single vortex tables, in the storage precision of the arithmetic (T)
@@ -59,6 +63,7 @@ struct lbm_ace_ctx {
     double* step_part = nullptr; int n_step_part = 0;
     double* red_part = nullptr; int n_red_part = 0;
     double* result = nullptr;
+    double* hres = nullptr; // pinned host copy of the result block (small, fast read-back)
     double* scratch = nullptr; size_t scratch_elems = 0; // FP64 staging for state/phi copies
     VelState vel;
     long long t = 0;
@@ -66,6 +71,7 @@ struct lbm_ace_ctx {
     bool fresh = true;      // next step is the first after init or a restart: d_t(phi u) = 0
     int rows = 0, grid_x = 0, grid_y = 0;
     int variant = 1;        // 1: ace_step (direct loads), 2: ace_step_bulk
+    int dev4_ctas = 3;      // resident CTAs per SM the 16-bit quad kernel is compiled for
     int tile_x = TILE_X;
     size_t smem = 0;        // dynamic shared memory of the chosen step kernel
     int* dev_err = nullptr; // set by a kernel whose bounded wait gave up (inside the result block)
@@ -235,8 +241,10 @@ void launch_dev_k(lbm_ace_ctx* c, const Vel& vel)
 {
     dim3 grid(c->grid_x, c->grid_y);
     StepArgs<float> a = make_args<float>(c);
-    if (c->variant == 7)
-        launch_pdl_smem(ace_step_dev4<S, MODEL, Vel>, grid, QUAD_THREADS, c->smem, c->stream, make_dev<S>(c), a, vel);
+    if (c->variant == 7 && c->dev4_ctas == 4)
+        launch_pdl_smem(ace_step_dev4<S, MODEL, Vel, 4>, grid, QUAD_THREADS, c->smem, c->stream, make_dev<S>(c), a, vel);
+    else if (c->variant == 7)
+        launch_pdl_smem(ace_step_dev4<S, MODEL, Vel, 3>, grid, QUAD_THREADS, c->smem, c->stream, make_dev<S>(c), a, vel);
     else
         launch_pdl(ace_step_dev<S, MODEL, Vel>, grid, PAIR_THREADS, c->stream, make_dev<S>(c), a, vel);
 }
@@ -447,7 +455,9 @@ template <typename S, int MODEL, class Vel>
 int occupancy_dev_k(lbm_ace_ctx* c, int* blocks)
 {
     if (c->variant == 7) {
-        auto k = ace_step_dev4<S, MODEL, Vel>;
+        // 4 CTAs/SM above 2^23 nodes (measured faster at 4096^2), 3 below (faster at 2048^2)
+        c->dev4_ctas = (long long)c->p.nx * c->p.ny > (1LL << 23) ? 4 : 3;
+        auto k = c->dev4_ctas == 4 ? ace_step_dev4<S, MODEL, Vel, 4> : ace_step_dev4<S, MODEL, Vel, 3>;
         c->smem = sizeof(QuadSmem);
         c->tile_x = QUAD_COLS;
         CK(c, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem));
@@ -513,13 +523,12 @@ int callback_upload(lbm_ace_ctx* c, double t, int pair)
 
 int check_device_error(lbm_ace_ctx* c);
 
-int finalize_sum(lbm_ace_ctx* c, const double* part, int n, double* out)
+// The sum in the result block and the wait-failure flag right after it, in one copy.
+int fetch_result(lbm_ace_ctx* c, double* out)
 {
-    // one copy brings back the sum and the wait-failure flag that sits right after it
-    ace_finalize<<<1, RED_THREADS, 0, c->stream>>>(part, n, c->result);
     CK(c, cudaGetLastError());
-    double back[3];
-    CK(c, cudaMemcpyAsync(back, c->result, sizeof back, cudaMemcpyDeviceToHost, c->stream));
+    double* back = c->hres;
+    CK(c, cudaMemcpyAsync(back, c->result, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
     int e;
     std::memcpy(&e, &back[2], sizeof e);
@@ -530,6 +539,12 @@ int finalize_sum(lbm_ace_ctx* c, const double* part, int n, double* out)
     }
     *out = back[0];
     return LBM_ACE_OK;
+}
+
+int finalize_sum(lbm_ace_ctx* c, const double* part, int n, double* out)
+{
+    ace_finalize<<<1, RED_THREADS, 0, c->stream>>>(part, n, c->result);
+    return fetch_result(c, out);
 }
 
 // After a stream synchronisation: report (and clear) a bounded wait that gave up.
@@ -586,6 +601,13 @@ int phi_to_scratch(lbm_ace_ctx* c)
     }
     CK(c, cudaGetLastError());
     return LBM_ACE_OK;
+}
+
+// Smallest index k with v[k] not finite, into *first (which starts at ULLONG_MAX).
+__global__ void ace_first_nonfinite(const double* __restrict__ v, long long n, unsigned long long* first)
+{
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
+        if (!isfinite(v[k])) atomicMin(first, (unsigned long long)k);
 }
 
 __global__ void ace_narrow(const double* __restrict__ in, float* __restrict__ out, long long n)
@@ -671,6 +693,7 @@ void lbm_ace_destroy(lbm_ace_ctx* c)
                     c->vel.sx2, c->vel.s2x, c->vel.sy2, c->vel.s2y,
                     c->vel.pu[0], c->vel.pu[1], c->vel.pv[0], c->vel.pv[1]};
     for (void* b : bufs) if (b) cudaFree(b);
+    if (c->hres) cudaFreeHost(c->hres);
     delete c;
 }
 
@@ -695,11 +718,13 @@ static int init_impl(lbm_ace_ctx* c, const lbm_ace_params* p)
         CK(c, cudaMalloc(&c->phi, n * c->elem));
     }
     if (p->kernel_variant == 6) CK(c, cudaMalloc(&c->phi_alt, n * sizeof(float)));
-    // result block: the reduced sum, a spare double, then the device wait-failure flag
+    // result block: the reduced sum, a spare double, the device wait-failure flag, and the
+    // ticket counter of the mass reductions that finish in their last CTA
     CK(c, cudaMalloc(&c->result, 4 * sizeof(double)));
     c->dev_err = reinterpret_cast<int*>(c->result + 2);
 
     CK(c, cudaMemset(c->result, 0, 4 * sizeof(double)));
+    CK(c, cudaMallocHost(&c->hres, 4 * sizeof(double)));
 
     // kernel variant: the bulk-copy pipeline needs 16-byte aligned rows
     // automatic choice: column pairs when nx is even (fastest measured on GB300 at
@@ -772,8 +797,14 @@ static int init_impl(lbm_ace_ctx* c, const lbm_ace_params* p)
     // initial phi: host array or the disk
     rc = ensure_scratch(c, n);
     if (rc) return rc;
+    unsigned long long* first_bad = reinterpret_cast<unsigned long long*>(c->result + 1);
+    const bool check_on_device = p->phi0 && n > kHostCheckMax;
     if (p->phi0) {
         CK(c, cudaMemcpyAsync(c->scratch, p->phi0, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+        if (check_on_device) { // large phi0: checked where it already is, instead of a host pass over it
+            CK(c, cudaMemsetAsync(first_bad, 0xff, sizeof(unsigned long long), c->stream));
+            ace_first_nonfinite<<<grid_for((long long)n, c->sms), 256, 0, c->stream>>>(c->scratch, (long long)n, first_bad);
+        }
     } else {
         std::vector<double> h(n);
         for (int y = 0; y < ny; ++y)
@@ -795,6 +826,13 @@ static int init_impl(lbm_ace_ctx* c, const lbm_ace_params* p)
     }
     c->fresh = true;
     CK(c, cudaGetLastError());
+    if (check_on_device) {
+        unsigned long long bad = 0;
+        CK(c, cudaMemcpyAsync(&bad, first_bad, sizeof bad, cudaMemcpyDeviceToHost, c->stream));
+        CK(c, cudaStreamSynchronize(c->stream));
+        if (bad != ~0ULL) return fail(c, LBM_ACE_EINVAL, "phi0[%llu] is not finite", bad);
+        CK(c, cudaMemsetAsync(first_bad, 0, sizeof(unsigned long long), c->stream));
+    }
     CK(c, cudaStreamSynchronize(c->stream));
     return LBM_ACE_OK;
 }
@@ -844,12 +882,12 @@ int lbm_ace_init(const lbm_ace_params* p, lbm_ace_ctx** out)
         break;
     default: return fail(nullptr, LBM_ACE_EINVAL, "velocity kind %d unknown", p->velocity_kind);
     }
-    if (p->phi0) {
+    if (p->phi0 && (size_t)p->nx * p->ny <= kHostCheckMax) { // larger fields are checked on the device
         const size_t n = (size_t)p->nx * p->ny;
         for (size_t k = 0; k < n; ++k)
             if (!std::isfinite(p->phi0[k]))
                 return fail(nullptr, LBM_ACE_EINVAL, "phi0[%zu] is not finite", k);
-    } else if (!std::isfinite(p->xc) || !std::isfinite(p->yc) || !std::isfinite(p->R)) {
+    } else if (!p->phi0 && (!std::isfinite(p->xc) || !std::isfinite(p->yc) || !std::isfinite(p->R))) {
         return fail(nullptr, LBM_ACE_EINVAL, "disk centre/radius not finite");
     }
     if (p->rows_per_cta < 0) return fail(nullptr, LBM_ACE_EINVAL, "rows_per_cta must be >= 0");
@@ -1021,18 +1059,29 @@ int lbm_ace_mass(lbm_ace_ctx* c, double* out)
     DeviceGuard g(c->dev);
     const long long n = (long long)c->p.nx * c->p.ny, n9 = 9 * n;
     const unsigned short* gs = (const unsigned short*)c->f[c->cur];
+    unsigned* done = reinterpret_cast<unsigned*>(c->result + 3);
+    int rc;
     switch (c->p.precision) {
-    case LBM_ACE_F64: ace_sum_partials<double><<<c->n_red_part, RED_THREADS, 0, c->stream>>>((const double*)c->f[c->cur], n9, c->red_part); break;
-    case LBM_ACE_F32: ace_sum_partials_f32<<<c->n_red_part, RED_THREADS, 0, c->stream>>>((const float*)c->f[c->cur], n9, c->red_part); break;
+    case LBM_ACE_F64:
+        ace_sum_partials<double><<<c->n_red_part, RED_THREADS, 0, c->stream>>>((const double*)c->f[c->cur], n9, c->red_part);
+        rc = finalize_sum(c, c->red_part, c->n_red_part, out);
+        break;
+    case LBM_ACE_F32:
+        ace_sum_partials_f32<<<c->n_red_part, RED_THREADS, 0, c->stream>>>((const float*)c->f[c->cur], n9, c->red_part,
+                                                                           done, c->result);
+        rc = fetch_result(c, out);
+        break;
     case LBM_ACE_F16DEV:
-        ace_sum_partials_dev<__half><<<c->n_red_part, RED_THREADS, 0, c->stream>>>(gs, c->phi2[c->pcur], n, c->red_part);
+        ace_sum_partials_dev<__half><<<c->n_red_part, RED_THREADS, 0, c->stream>>>(gs, c->phi2[c->pcur], n, c->red_part,
+                                                                                   done, c->result);
+        rc = fetch_result(c, out);
         break;
     default:
-        ace_sum_partials_dev<__nv_bfloat16><<<c->n_red_part, RED_THREADS, 0, c->stream>>>(gs, c->phi2[c->pcur], n, c->red_part);
+        ace_sum_partials_dev<__nv_bfloat16><<<c->n_red_part, RED_THREADS, 0, c->stream>>>(gs, c->phi2[c->pcur], n,
+                                                                                          c->red_part, done, c->result);
+        rc = fetch_result(c, out);
         break;
     }
-    CK(c, cudaGetLastError());
-    const int rc = finalize_sum(c, c->red_part, c->n_red_part, out);
     if (rc) return rc;
     if (!std::isfinite(*out)) return fail(c, LBM_ACE_ENUMERIC, "global mass is not finite (%g)", *out);
     return LBM_ACE_OK;

@@ -59,11 +59,12 @@ struct BatchCtl {
     int active_next; // the same for time t + 1, filled in by ace_batch_phase
 };
 
+// Tile (bx, by) of lattice I at time t with tiles `rows` tall; the tile's mass partial
+// goes to *mass_out.
 template <int MODEL>
-__device__ __forceinline__ void batch_tile(const BatchInst& I, float2 ph, int lt, int t, float (*chi_s)[PAIR_COLS + 4],
-                                           double* red_s)
+__device__ __forceinline__ void batch_tile_at(const BatchInst& I, float2 ph, int bx, int by, int rows, int t,
+                                              float (*chi_s)[PAIR_COLS + 4], double* red_s, double* mass_out)
 {
-    const int bx = lt % I.tiles_x, by = lt / I.tiles_x;
     StepArgs<float> a;
     a.fin = I.f[t & 1];
     a.fout = I.f[(t & 1) ^ 1];
@@ -71,7 +72,7 @@ __device__ __forceinline__ void batch_tile(const BatchInst& I, float2 ph, int lt
     a.mass_part = I.mass_part;
     a.nx = I.nx; a.ny = I.ny;
     a.plane = (long long)I.nx * I.ny;
-    a.rows = I.rows;
+    a.rows = rows;
     a.first = t == 0;
     a.tdir = t & 1; // unused by pair_tile's default downward march
     a.omega = I.omega; a.fpref = I.fpref;
@@ -82,7 +83,15 @@ __device__ __forceinline__ void batch_tile(const BatchInst& I, float2 ph, int lt
     vel.amp = I.amp;
     vel.ct = ph.x;
     vel.ctm1 = ph.y;
-    pair_tile<float, MODEL>(a, vel, bx * PAIR_COLS, by * I.rows, chi_s, red_s, &I.mass_part[lt]);
+    pair_tile<float, MODEL>(a, vel, bx * PAIR_COLS, by * rows, chi_s, red_s, mass_out);
+}
+
+// Work item lt (row-major over the lattice's tiles of the batch's height I.rows).
+template <int MODEL>
+__device__ __forceinline__ void batch_tile(const BatchInst& I, float2 ph, int lt, int t, float (*chi_s)[PAIR_COLS + 4],
+                                           double* red_s)
+{
+    batch_tile_at<MODEL>(I, ph, lt % I.tiles_x, lt / I.tiles_x, I.rows, t, chi_s, red_s, &I.mass_part[lt]);
 }
 
 template <int MODEL>
@@ -106,16 +115,20 @@ ace_batch_step(const BatchInst* __restrict__ inst, const float2* __restrict__ ph
     }
 }
 
-// One launch per lattice (the per-lattice baseline): CTA b runs tile first + b of the
-// work list, with the same tile code and device-side phases as the persistent kernel.
+// One launch per lattice (the per-lattice baseline): a grid over lattice i in the launch
+// shape the single-lattice library picks (tiles `rows` tall), with the same tile code
+// and device-side phases as the persistent kernel; mass partials go to a scratch array.
 template <int MODEL>
 __global__ void __launch_bounds__(PAIR_THREADS, 5)
-ace_batch_one(const BatchInst* __restrict__ inst, const float2* __restrict__ phase, int i, const BatchCtl* ctl)
+ace_batch_one(const BatchInst* __restrict__ inst, const float2* __restrict__ phase, int i, int rows,
+              const BatchCtl* ctl, double* part)
 {
     __shared__ __align__(16) float chi_s[4][PAIR_COLS + 4];
     __shared__ double red_s[PAIR_THREADS / 32];
     const int t = ctl->t;
-    if (t < inst[i].end) batch_tile<MODEL>(inst[i], phase[i], blockIdx.x, t, chi_s, red_s);
+    if (t < inst[i].end)
+        batch_tile_at<MODEL>(inst[i], phase[i], blockIdx.x, blockIdx.y, rows, t, chi_s, red_s,
+                             &part[blockIdx.y * gridDim.x + blockIdx.x]);
 }
 
 // For the next step, t + 1: the phase of Eq. 14, (cos(pi (t+1) / T), cos(pi t / T)), per
@@ -258,19 +271,21 @@ void launch_batch_step(lbm_ace_batch* b)
     ace_batch_tick<<<1, 1, 0, b->stream>>>(b->ctl);
 }
 
-// The per-lattice baseline: one launch per lattice (all of its tiles, the batch's tile
-// heights), then the same phase and tick kernels. Lattices past their end launch
-// nothing but a no-op grid of their tiles, as a per-lattice scheduler would skip them
-// only on the host.
+// The per-lattice baseline: one launch per lattice in the single-lattice library's launch
+// shape, then the same phase and tick kernels. A lattice past its end still launches,
+// and its CTAs return at once.
 void launch_per_lattice_step(lbm_ace_batch* b)
 {
     for (int i = 0; i < b->n; ++i) {
         const BatchInst& I = b->inst[i];
-        const int tiles = I.tiles_x * I.tiles_y;
+        const int rows = b->seq_rows[i];
+        const dim3 grid(I.tiles_x, (I.ny + rows - 1) / rows);
         if (b->model == LBM_ACE_MODEL_MODIFIED)
-            ace_batch_one<MODEL_MODIFIED><<<tiles, PAIR_THREADS, 0, b->stream>>>(b->d_inst, b->phase, i, b->ctl);
+            ace_batch_one<MODEL_MODIFIED><<<grid, PAIR_THREADS, 0, b->stream>>>(b->d_inst, b->phase, i, rows, b->ctl,
+                                                                             b->seq_part);
         else
-            ace_batch_one<MODEL_CONSERVATIVE><<<tiles, PAIR_THREADS, 0, b->stream>>>(b->d_inst, b->phase, i, b->ctl);
+            ace_batch_one<MODEL_CONSERVATIVE><<<grid, PAIR_THREADS, 0, b->stream>>>(b->d_inst, b->phase, i, rows,
+                                                                                 b->ctl, b->seq_part);
     }
     ace_batch_phase<<<(b->n + 255) / 256, 256, 0, b->stream>>>(b->ctl, b->d_inst, b->n, b->d_end_sorted, b->d_prefix,
                                                               b->phase);
@@ -426,7 +441,8 @@ int lbm_ace_batch_init(const lbm_ace_params* params, int count, lbm_ace_batch** 
     BI(cudaMalloc(&b->phase, count * sizeof(float2)));
     BI(cudaMalloc(&b->d_end_sorted, count * sizeof(long long)));
     BI(cudaMalloc(&b->d_prefix, count * sizeof(int)));
-    BI(cudaMalloc(&b->result, 2 * sizeof(double)));
+    BI(cudaMalloc(&b->result, 2 * sizeof(double))); // the mass, then the reduction's ticket counter
+    BI(cudaMemset(b->result, 0, 2 * sizeof(double)));
     long long maxn = 0;
     for (const auto& q : b->p) maxn = std::max(maxn, (long long)q.nx * q.ny);
     b->n_red = (int)std::min<long long>((9 * maxn + 255) / 256, (long long)b->sms * 8);
@@ -717,8 +733,8 @@ int lbm_ace_batch_mass(lbm_ace_batch* b, int i, double* out)
     if (!out) return bfail(b, LBM_ACE_EINVAL, "out is NULL");
     const BatchInst& I = b->inst[i];
     const long long n9 = 9LL * I.nx * I.ny;
-    ace_sum_partials_f32<<<b->n_red, RED_THREADS, 0, b->stream>>>(I.f[std::min(b->t, I.end) & 1], n9, b->red_part);
-    ace_finalize<<<1, RED_THREADS, 0, b->stream>>>(b->red_part, b->n_red, b->result);
+    ace_sum_partials_f32<<<b->n_red, RED_THREADS, 0, b->stream>>>(I.f[std::min(b->t, I.end) & 1], n9, b->red_part,
+                                                                  reinterpret_cast<unsigned*>(b->result + 1), b->result);
     BK(b, cudaGetLastError());
     BK(b, cudaMemcpyAsync(out, b->result, sizeof(double), cudaMemcpyDeviceToHost, b->stream));
     BK(b, cudaStreamSynchronize(b->stream));

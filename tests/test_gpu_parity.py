@@ -361,3 +361,19 @@ def test_kernel_variants_are_bit_identical(L, precision):
             out.append(g.get_state())
     for o in out[1:]:
         assert np.array_equal(out[0][0], o[0]) and np.array_equal(out[0][1], o[1])
+
+
+@pytest.mark.parametrize("k", [0, 12345, 300 * 300 - 1])
+def test_large_non_finite_phi0_is_rejected_after_upload(k):
+    """phi0 fields above 65,536 values are checked on the device right after their
+    upload (small ones on the host): the smallest bad index is reported as EINVAL, and a
+    valid field then builds a working lattice."""
+    phi0 = np.full((300, 300), 0.5)
+    phi0.flat[k] = np.inf if k % 2 else np.nan
+    phi0.flat[min(k + 7, phi0.size - 1)] = np.nan
+    with pytest.raises(A.LbmAceError) as e:
+        A.Lattice(nx=300, ny=300, phi0=phi0, precision=A.F32)
+    assert e.value.status == A.EINVAL and f"phi0[{k}]" in str(e.value)
+    with A.Lattice(nx=300, ny=300, phi0=np.full((300, 300), 0.5), precision=A.F32) as g:
+        g.step(3)
+        assert g.mass() == pytest.approx(0.5 * 300 * 300, rel=1e-6)  # FP32 populations
