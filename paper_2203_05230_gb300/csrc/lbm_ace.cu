@@ -726,10 +726,7 @@ static int init_impl(lbm_ace_ctx* c, const lbm_ace_params* p)
     CK(c, cudaMemset(c->result, 0, 4 * sizeof(double)));
     CK(c, cudaMallocHost(&c->hres, 4 * sizeof(double)));
 
-    // kernel variant: the bulk-copy pipeline needs 16-byte aligned rows
-    // automatic choice: column pairs when nx is even (fastest measured on GB300 at
-    // 2048^2), else direct loads
-    // automatic choice, measured on GB300 (FP32): four columns per thread in warp strips
+    // kernel variant, automatic choice measured on GB300 (FP32): four columns per thread in warp strips
     // up to 2^23 nodes (1024^2: 71k against 67k MLUPS for column pairs; 2048^2: 80k against
     // 79k), column pairs above (4096^2: 82k against 80k), direct loads for odd nx; FP64:
     // column pairs for even nx

@@ -8,8 +8,15 @@ FP64 erf, and the rare BF16 rounding that the two land on opposite sides of (a 2
 relative change of one stored value). For 288-term dot products the FP32 error is
 ~1e-6 of the terms, so a flip happens for ~5e-4 of the stored values; four layers of
 such flips move the result by ~2e-4 relative (L2), hence 2e-3 for the forward increment
-and 1e-2 for the gradients (whose last reduction runs over all pixels). Against the
-pure FP64 oracle the BF16 storage itself shows; 5e-2 bounds it.
+and 1e-2 for the gradients (whose last reduction runs over all pixels).
+
+Against the pure FP64 oracle the BF16 storage itself shows. A stored value carries a
+relative rounding error of at most 2^-9 (about 1.1e-3 RMS). A forward pass stores at
+about eight points (the weights of layers 2-4, z and a of layers 1-4), so independent
+errors give sqrt(8) x 1.1e-3 = 3e-3 relative, somewhat amplified by the layers after
+them. The oracle's own emulate mode measures 4-6e-3 for the forward increment and 4-8e-3
+for the gradients on these problems. The GPU adds at most the 2e-3 / 5e-3 above, hence
+1e-2 and 1.5e-2.
 """
 import math
 
@@ -66,7 +73,7 @@ def test_forward_matches_oracle(net, B, H, Wd):
     emu, _ = S.forward(flat, phi, u, v, emulate=True)
     exact, _ = S.forward(flat, phi, u, v)
     assert rel(got - phi, emu - phi) < 2e-3
-    assert rel(got - phi, exact - phi) < 5e-2
+    assert rel(got - phi, exact - phi) < 1e-2
     assert np.allclose(got.sum(axis=(1, 2)), phi.sum(axis=(1, 2)), rtol=2e-6, atol=1e-4)
 
 
@@ -87,7 +94,7 @@ def test_gradient_matches_oracle(net, B, H, Wd):
         assert d < 1e-2 * np.linalg.norm(ge[k:k + n]) + 1e-6 * gn, (shp, k)
         k += n
     assert rel(g, ge) < 5e-3
-    assert rel(g, gx) < 5e-2
+    assert rel(g, gx) < 1.5e-2
 
 
 def test_adam_matches_oracle(net):

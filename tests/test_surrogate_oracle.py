@@ -153,10 +153,12 @@ def test_emulated_storage_error_is_bf16_sized():
     b, _ = S.forward(flat, phi, u, v, emulate=True)
     d, db = a - phi, b - phi
     rel = np.sqrt(((d - db) ** 2).sum() / (d ** 2).sum())
-    assert 1e-5 < rel < 3e-2
+    assert 1e-3 < rel < 1e-2
     _, ga, _ = S.loss_and_grad(flat, phi, u, v, tgt)
     _, gb, _ = S.loss_and_grad(flat, phi, u, v, tgt, emulate=True)
-    assert np.linalg.norm(ga - gb) < 5e-2 * np.linalg.norm(ga)
+    # BF16 storage at about eight points of the pass: 5.5e-3 (forward) and 6.7e-3
+    # (gradient) measured here, sqrt(8) x 2^-9 / sqrt(3) = 3.2e-3 before amplification
+    assert np.linalg.norm(ga - gb) < 1.5e-2 * np.linalg.norm(ga)
 
 
 def test_adam_first_step_closed_form():
