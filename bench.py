@@ -43,6 +43,12 @@ KERNEL_NAME = {1: "ace_step", 2: "ace_step_bulk", 3: "ace_step_warp", 4: "ace_st
                6: "ace_step_tb2", 7: "ace_step_dev4", 8: "ace_step_quad"}
 STEPS_PER_LAUNCH = {6: 2}   # the two-step kernel: one launch advances two steps
 BYTES_PER_LUP = {"f64": 160, "f32": 80, "f16dev": 44, "bf16dev": 44}
+# FP64 step: 204 FP64 FLOP per node update (55.5 DFMA counted twice, 53.4 DADD, 40.0 DMUL;
+# ncu op counters of ace_step_pair<double>), bound by the FP64 pipe rather than by HBM.
+# Peak: GB300's nominal FP64 rate, 152 SMs x 2.07 GHz x 4 FLOP per clock = 1.259 TFLOP/s
+# (an FMA-chain probe measured 1.256).
+F64_FLOP_PER_LUP = 204.0
+F64_PEAK_TFLOPS = 152 * 2.07e9 * 4 / 1e12
 L2_NOTE = "inputs larger than L2: 2 x 151 MB FP32 population buffers + 16.8 MB phi plane"
 
 
@@ -176,10 +182,11 @@ def rejected(clk):
 
 
 def kernel_source_hash() -> str:
-    """Hash of the step kernels' device sources (all variants)."""
+    """Hash of the step kernels' device sources (all variants; the mass reductions of
+    ace_reduce.cuh are not part of a step)."""
     h = hashlib.sha256()
     for name in ("ace_kernels.cuh", "ace_step_bulk.cuh", "ace_step_warp.cuh", "ace_step_pair.cuh",
-                 "ace_step_dev.cuh", "ace_step_dev4.cuh", "ace_step_quad.cuh"):
+                 "ace_step_dev.cuh", "ace_step_dev4.cuh", "ace_step_quad.cuh", "ace_step_tb2.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2203_05230_gb300", "csrc", name), "rb").read())
     return h.hexdigest()[:16]
 
@@ -328,6 +335,20 @@ def run_ours(args):
     achieved = bpl / per_launch / 1e9
     traffic = stored_traffic(KERNEL_NAME[shape[4]], args.precision, args.L)
     lat.close()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+                else "fallback",
+                "algorithmic_bytes_per_launch": bpl, "lattice_updates_per_launch": spl * args.L * args.L,
+                "kernel": "lbmace::" + KERNEL_NAME[shape[4]]}
+    if args.precision == "f64":  # bound by the FP64 pipe: FLOP/s against the FP64 rate
+        tf = F64_FLOP_PER_LUP * spl * args.L * args.L / per_launch / 1e12
+        roofline = {"bound": "alu", "achieved": tf, "peak": F64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": tf / F64_PEAK_TFLOPS, "traffic": traffic,
+                    "peak_kind": "derived: nominal FP64 rate, 152 SMs x 2.07 GHz x 4 FLOP/clk",
+                    "flop_per_lattice_update": F64_FLOP_PER_LUP,
+                    "hbm_frac_algorithmic": achieved / peak,
+                    "kernel": "lbmace::" + KERNEL_NAME[shape[4]]}
 
     e2e = None
     if not args.no_e2e:
@@ -348,12 +369,7 @@ def run_ours(args):
                                                     8: "ace_step_quad (four columns per thread, warp strips)"}[shape[4]],
                                          "steps_per_launch": spl},
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": traffic,
-                         "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
-                         else "fallback",
-                         "algorithmic_bytes_per_launch": bpl, "lattice_updates_per_launch": spl * args.L * args.L,
-                         "kernel": "lbmace::" + KERNEL_NAME[shape[4]]},
+            "roofline": roofline,
             "hbm_gbs_algorithmic": achieved,
             "mass_drift_rel_timed": (m1 - m0) / m0,
             "clocks": clk, "gpu_launches": launches, "e2e": e2e}

@@ -118,7 +118,9 @@ typedef struct lbm_ace_params {
     int device;          /* CUDA device ordinal */
     void* stream;        /* cudaStream_t for all device work; NULL = the legacy default stream */
     int rows_per_cta;    /* launch shape of the fused step: rows each CTA marches over;
-                            0 selects a default for the lattice size and the device */
+                            0 selects a default for the lattice size and the device;
+                            at most 4095 with kernel variants 7 and 8 (else
+                            LBM_ACE_EINVAL) */
     int kernel_variant;  /* fused step kernel: 0 = automatic (FP32 with nx a multiple of 4 and at
                             most 2^23 nodes: 8; else 4 for even nx, else 1), 1 = direct global
                             loads with a CTA-wide row barrier, 2 = rows staged in shared
@@ -158,9 +160,14 @@ int lbm_ace_step(lbm_ace_ctx* c, long long n);
  * host array out[count], count == nx*ny. Synchronous. */
 int lbm_ace_get_phi(lbm_ace_ctx* c, double* out, size_t count);
 
-/* Global mass sum_x sum_i f_i(x, t) of the current state, summed on the
- * device in FP64 with compensation in a fixed order (deterministic).
- * Synchronous. Returns LBM_ACE_ENUMERIC (with *out set) when it is not finite. */
+/* Global mass sum_x sum_i f_i(x, t) of the current state, summed on the device in
+ * a fixed order (deterministic). FP64 states: Neumaier-compensated FP64 sums. FP32 and
+ * 16-bit states: each value split into a multiple of 2^-16, summed exactly as an
+ * integer, and a remainder below 2^-17 summed in FP32 (a thread that meets a value of
+ * 2 or more in magnitude sums its values in FP64 instead), per-thread totals combined
+ * with a compensated FP64 tree; relative error about 1e-14. One kernel launch; the
+ * result reaches the host through mapped pinned memory. Synchronous. Returns
+ * LBM_ACE_ENUMERIC (with *out set) when it is not finite. */
 int lbm_ace_mass(lbm_ace_ctx* c, double* out);
 
 /* Global mass sum_x phi(x, t-1) as reduced block by block inside the last
@@ -307,8 +314,10 @@ void lbm_ace_batch_destroy(lbm_ace_batch* b); /* NULL-safe */
  *   values   device address of `count` values, FP64 (precision LBM_ACE_F64) or FP32
  *            (LBM_ACE_F32), e.g. the 9 population planes of a lattice or a phi field;
  *   out      device address of one double that receives the sum (0 for count == 0):
- *            the same Neumaier-compensated algorithm as lbm_ace_mass, in a fixed but
- *            different order, so the two agree to about 1e-15 relative, not bitwise;
+ *            a Neumaier-compensated FP64 sum of the values in a fixed order (for FP64
+ *            values the algorithm of lbm_ace_mass, in a different order; FP32 states
+ *            lbm_ace_mass sums in exact split parts), so the two agree to about 1e-14
+ *            relative, not bitwise;
  *   stream   cudaStream_t of the current device (NULL: legacy default stream).
  * The work is asynchronous on `stream` and runs on the current CUDA device. Both
  * pointers must be device memory of the current device (or managed memory); a host

@@ -560,177 +560,29 @@ __global__ void ace_push_state(const double* __restrict__ f, const double* __res
     }
 }
 
-// Neumaier-compensated accumulation.
-__device__ __forceinline__ void neumaier(double& s, double& c, double v)
+// Running sum of FP32 values split into a part rounded to a multiple of 2^-16, summed
+// exactly as an integer, and a remainder summed in FP32, two values at a time. It keeps
+// per-value sums on the FP32 and integer pipes (GB300 runs FP64 at 1/64 of the FP32
+// rate) and needs no flush inside a loop. For |v| < 64, t = v + 192 lies in [128, 256),
+// where consecutive FP32 values are 2^-16 apart; hence bits(t) - bits(192) =
+// (t - 192) * 2^16 exactly, t - 192 is v rounded to a multiple of 2^-16, and the
+// remainder v - (t - 192), below 2^-17, is exact as well. ai adds the raw bit patterns of
+// t modulo 2^32; with nv values added, ai - nv * bits(192) is the exact sum of the
+// rounded parts in units of 2^-16 while that sum stays below 2^15 in magnitude (8192
+// values below 2 each, say). The FP32 sum of the remainders carries the only rounding,
+// about 1e-14 of a lattice's total.
+__device__ __forceinline__ void split_add2i(unsigned& ai, float2& lo, float2 v)
 {
-    const double t = s + v;
-    c += fabs(s) >= fabs(v) ? (s - t) + v : (v - t) + s;
-    s = t;
-}
-
-constexpr int RED_THREADS = 256;
-
-// Partial sums of n values of T: each thread sums a fixed strided subset with
-// compensation, the CTA combines in a fixed tree order. Deterministic.
-template <typename T>
-__global__ void __launch_bounds__(RED_THREADS) ace_sum_partials(const T* __restrict__ v, long long n,
-                                                                double* __restrict__ part)
-{
-    __shared__ double sh[RED_THREADS];
-    double s = 0.0, c = 0.0;
-    for (long long k = blockIdx.x * (long long)RED_THREADS + threadIdx.x; k < n;
-         k += (long long)gridDim.x * RED_THREADS)
-        neumaier(s, c, (double)v[k]);
-    sh[threadIdx.x] = s + c;
-    __syncthreads();
-    for (int h = RED_THREADS / 2; h > 0; h >>= 1) {
-        if (threadIdx.x < h) sh[threadIdx.x] += sh[threadIdx.x + h];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
-}
-
-// Running sum of FP32 values in FP32 parts, two lanes at once: hi collects the values
-// rounded to multiples of 2^-16 (for |v| < 64, (v + 192) - 192 is that rounding and is
-// exact; a sum of such multiples is exact in FP32 while it stays below 256 in
-// magnitude), lo the remainders v - hi (exact, below 2^-17 in magnitude), whose own
-// FP32 sum carries the only rounding, ~1e-14 of the total. Callers flush hi and lo to
-// FP64 before hi can reach 256. It keeps per-value reductions on the FP32 pipes: GB300
-// runs FP64 at 1/64 of the FP32 rate.
-__device__ __forceinline__ void split_add2(float2& hi, float2& lo, float2 v)
-{
-    const float2 h = __fadd2_rn(__fadd2_rn(v, make_float2(192.0f, 192.0f)), make_float2(-192.0f, -192.0f));
-    hi = __fadd2_rn(hi, h);
+    const float2 t = __fadd2_rn(v, make_float2(192.0f, 192.0f));
+    const float2 h = __fadd2_rn(t, make_float2(-192.0f, -192.0f));
+    ai += __float_as_uint(t.x) + __float_as_uint(t.y);
     lo = __fadd2_rn(lo, __fadd2_rn(v, make_float2(-h.x, -h.y)));
 }
 
-__device__ __forceinline__ double split_flush(float2& hi, float2& lo)
+__device__ __forceinline__ double split_total_i(unsigned ai, float2 lo, unsigned nv)
 {
-    const double s = ((double)hi.x + (double)hi.y) + ((double)lo.x + (double)lo.y);
-    hi = lo = make_float2(0.0f, 0.0f);
-    return s;
-}
-
-// Mass accumulator of one thread over groups of four FP32 values: groups whose values
-// are all below 2 in magnitude (every population and phi of a lattice in practice) go
-// through split_add2 and are flushed every 32 groups (|hi| < 128); any other group is
-// added in FP64.
-struct MassAcc4 {
-    float2 hi = make_float2(0.0f, 0.0f), lo = make_float2(0.0f, 0.0f);
-    double d = 0.0;
-    int n = 0;
-    __device__ __forceinline__ void add(float4 q)
-    {
-        const float m = fmaxf(fmaxf(fabsf(q.x), fabsf(q.y)), fmaxf(fabsf(q.z), fabsf(q.w)));
-        if (m < 2.0f) {
-            split_add2(hi, lo, make_float2(q.x, q.y));
-            split_add2(hi, lo, make_float2(q.z, q.w));
-            if (++n == 32) {
-                d += split_flush(hi, lo);
-                n = 0;
-            }
-        } else {
-            d += ((double)q.x + (double)q.y) + ((double)q.z + (double)q.w);
-        }
-    }
-    __device__ __forceinline__ double total() { return d + split_flush(hi, lo); }
-};
-
-// Fixed-order CTA sum of one double per thread into part[blockIdx.x].
-__device__ __forceinline__ void block_sum_to(double v, double* sh, double* part)
-{
-    sh[threadIdx.x] = v;
-    __syncthreads();
-    for (int h = RED_THREADS / 2; h > 0; h >>= 1) {
-        if (threadIdx.x < h) sh[threadIdx.x] += sh[threadIdx.x + h];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
-}
-
-// Fixed-order compensated sum of part[0 .. n) by the CTA's RED_THREADS threads: each a
-// Neumaier sum over a strided subset, then a pairwise tree whose nodes add two
-// (sum, compensation) pairs with an error-free two-sum of the sums. Returns the total
-// in thread 0.
-__device__ __forceinline__ double block_final_sum(const double* part, int n, double* ss, double* sc)
-{
-    double s = 0.0, c = 0.0;
-    for (int k = threadIdx.x; k < n; k += RED_THREADS) neumaier(s, c, part[k]);
-    ss[threadIdx.x] = s;
-    sc[threadIdx.x] = c;
-    __syncthreads();
-    for (int h = RED_THREADS / 2; h > 0; h >>= 1) {
-        if (threadIdx.x < h) {
-            const double a = ss[threadIdx.x], b = ss[threadIdx.x + h];
-            const double t = a + b;
-            const double bp = t - a;
-            const double err = (a - (t - bp)) + (b - bp); // two-sum: a + b = t + err exactly
-            ss[threadIdx.x] = t;
-            sc[threadIdx.x] += sc[threadIdx.x + h] + err;
-        }
-        __syncthreads();
-    }
-    return ss[0] + sc[0];
-}
-
-// After every CTA has written its partial: the CTA that finishes last (a ticket counter
-// in global memory, zero between calls) sums all partials in their fixed order into
-// *out and resets the counter. Saves the separate finishing launch; the result does not
-// depend on which CTA finishes last.
-__device__ __forceinline__ void finish_in_last_block(const double* part, unsigned* done, double* out, double* ss,
-                                                     double* sc)
-{
-    __shared__ bool last;
-    if (threadIdx.x == 0) {
-        __threadfence(); // this CTA's partial is visible before its ticket
-        last = atomicAdd(done, 1u) == gridDim.x - 1;
-    }
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    const double total = block_final_sum(part, gridDim.x, ss, sc);
-    if (threadIdx.x == 0) {
-        out[0] = total;
-        *done = 0u;
-    }
-}
-
-// Partial sums of n FP32 values (16-byte aligned) for the global mass: 16-byte loads,
-// MassAcc4 per thread over a fixed strided subset of the groups of four, the n % 4 last
-// values in FP64 by the first threads of CTA 0, then a fixed tree per CTA.
-// Deterministic, bound by HBM bandwidth rather than by the FP64 pipe.
-static __global__ void __launch_bounds__(RED_THREADS) ace_sum_partials_f32(const float* __restrict__ v, long long n,
-                                                                           double* __restrict__ part,
-                                                                           unsigned* done, double* out)
-{
-    __shared__ double sh[RED_THREADS], sc[RED_THREADS];
-    const float4* v4 = reinterpret_cast<const float4*>(v);
-    const long long n4 = n >> 2;
-    const long long stride = (long long)gridDim.x * RED_THREADS;
-    MassAcc4 acc;
-    long long k = blockIdx.x * (long long)RED_THREADS + threadIdx.x;
-    for (; k + 3 * stride < n4; k += 4 * stride) { // four independent 16-byte loads in flight
-        const float4 q0 = v4[k], q1 = v4[k + stride], q2 = v4[k + 2 * stride], q3 = v4[k + 3 * stride];
-        acc.add(q0);
-        acc.add(q1);
-        acc.add(q2);
-        acc.add(q3);
-    }
-    for (; k < n4; k += stride) acc.add(v4[k]);
-    double s = acc.total();
-    if (blockIdx.x == 0 && threadIdx.x < (n & 3)) s += (double)v[4 * n4 + threadIdx.x];
-    block_sum_to(s, sh, part);
-    finish_in_last_block(part, done, out, sh, sc);
-}
-
-// Final sum of n partials by one CTA (block_final_sum), for partials written by kernels
-// that do not finish their own sums.
-static __global__ void __launch_bounds__(RED_THREADS) ace_finalize(const double* __restrict__ part, int n,
-                                                                   double* __restrict__ out)
-{
-    __shared__ double ss[RED_THREADS], sc[RED_THREADS];
-    const double total = block_final_sum(part, n, ss, sc);
-    if (threadIdx.x == 0) out[0] = total;
+    const int m = (int)(ai - nv * 0x43400000u); // 0x43400000 = bits(192.0f)
+    return (double)m * 0x1p-16 + ((double)lo.x + (double)lo.y);
 }
 
 } // namespace lbmace

@@ -369,37 +369,4 @@ __global__ void ace_push_state_dev(const double* __restrict__ f, const double* _
     }
 }
 
-// Partial sums of the stored state's mass: the 9 deviation planes (n16 16-bit values,
-// 8-byte aligned) plus the phi plane (n values, FP32, 16-byte aligned); the split
-// weights sum to 1, so sum_i f_i = sum_i g_i + phi at every node. Groups of four values
-// are widened exactly to FP32 and summed by MassAcc4, the ragged ends in FP64 by the
-// first threads of CTA 0; a fixed tree per CTA. Deterministic.
-template <typename S>
-__global__ void __launch_bounds__(RED_THREADS) ace_sum_partials_dev(const unsigned short* __restrict__ g,
-                                                                    const float* __restrict__ phi, long long n,
-                                                                    double* __restrict__ part, unsigned* done,
-                                                                    double* out)
-{
-    using C = Dev16<S>;
-    __shared__ double sh[RED_THREADS], sc[RED_THREADS];
-    const long long n16 = 9 * n;
-    const uint2* g4 = reinterpret_cast<const uint2*>(g);
-    const float4* p4 = reinterpret_cast<const float4*>(phi);
-    const long long stride = (long long)gridDim.x * RED_THREADS;
-    const long long first = blockIdx.x * (long long)RED_THREADS + threadIdx.x;
-    MassAcc4 acc;
-    for (long long k = first; k < (n16 >> 2); k += stride) {
-        const uint2 q = g4[k];
-        acc.add(make_float4(C::lo(q.x), C::hi(q.x), C::lo(q.y), C::hi(q.y)));
-    }
-    for (long long k = first; k < (n >> 2); k += stride) acc.add(p4[k]);
-    double s = acc.total();
-    if (blockIdx.x == 0) {
-        if (threadIdx.x < (n16 & 3)) s += (double)C::one(g[4 * (n16 >> 2) + threadIdx.x]);
-        if (threadIdx.x < (n & 3)) s += (double)phi[4 * (n >> 2) + threadIdx.x];
-    }
-    block_sum_to(s, sh, part);
-    finish_in_last_block(part, done, out, sh, sc);
-}
-
 } // namespace lbmace

@@ -26,11 +26,15 @@
 //   * The row loop is not unrolled: an unrolled body (to rotate the rolling window of
 //     phi(t-1) rows without register moves) overflowed the instruction cache, which cost
 //     far more than the moves.
-//   * The mass partial of phi(t) is accumulated exactly in FP32 (split_add2, flushed to
-//     FP64 every 64 rows), keeping the FP64 pipe, 1/64 of the FP32 rate on GB300, off
-//     the row loop.
+//   * The mass partial of phi(t) is accumulated in FP32 parts whose rounded part is an
+//     exact integer sum (split_add2i), keeping the FP64 pipe, 1/64 of the FP32 rate on
+//     GB300, off the row loop. An FP64 flush every 64 rows under a counter test was
+//     predicated into every row iteration by the compiler: 2 FP64-pipe instructions per
+//     node, the FP64 pipe 36 % busy; without it, 4096^2 BF16 went from 105.5k to 110.5k
+//     MLUPS and 2048^2 from 94.7k to 98.0k.
 //
-// Requirement (checked by the host): nx a multiple of 4.
+// Requirements (checked by the host): nx a multiple of 4; at most 4095 rows per CTA
+// (the integer part of the mass partial is exact for up to 4 x 4095 values below 2).
 #pragma once
 
 #include "ace_step_dev.cuh"
@@ -159,9 +163,9 @@ __device__ __forceinline__ void dev4_tile(const DevArgs<S>& d, const StepArgs<fl
         unpack_phi(q, Wc);
     }
     float4 php = make_float4(0.0f, 0.0f, 0.0f, 0.0f); // phi(t) of the row that collides next
-    float2 mhi = make_float2(0.0f, 0.0f), mlo = make_float2(0.0f, 0.0f);
-    double md = 0.0;
-    int mrows = 0;
+    float2 mlo = make_float2(0.0f, 0.0f);
+    unsigned mai = 0u;
+    float mmax = 0.0f;
 
     auto body = [&](int k) {
         unpack_phi(pnx, Wa);
@@ -281,12 +285,9 @@ __device__ __forceinline__ void dev4_tile(const DevArgs<S>& d, const StepArgs<fl
 #pragma unroll
                 for (int i = 0; i < 9; ++i) gout[(o + (unsigned)i * plane) >> 2] = make_uint2(packed[0][i], packed[1][i]);
                 *reinterpret_cast<float4*>(d.phout + o) = php;
-                split_add2(mhi, mlo, make_float2(php.x, php.y));
-                split_add2(mhi, mlo, make_float2(php.z, php.w));
-                if (++mrows == 64) { // keep the exact FP32 sum of multiples of 2^-16 below 256
-                    md += split_flush(mhi, mlo);
-                    mrows = 0;
-                }
+                split_add2i(mai, mlo, make_float2(php.x, php.y));
+                split_add2i(mai, mlo, make_float2(php.z, php.w));
+                mmax = fmaxf(mmax, fmaxf(fmaxf(fabsf(php.x), fabsf(php.y)), fmaxf(fabsf(php.z), fabsf(php.w))));
             }
         }
         php = make_float4(s0.x, s0.y, s1.x, s1.y);
@@ -302,7 +303,16 @@ __device__ __forceinline__ void dev4_tile(const DevArgs<S>& d, const StepArgs<fl
         }
     }
 
-    double msum = md + split_flush(mhi, mlo);
+    double msum;
+    if (mmax < 2.0f) {
+        msum = split_total_i(mai, mlo, live && act ? 4u * (unsigned)(y1 - y0) : 0u);
+    } else { // a value of 2 or more: the FP64 sum of the phi this thread wrote
+        msum = 0.0;
+        for (int yc = y0; yc < y1; ++yc) {
+            const float4 q = *reinterpret_cast<const float4*>(d.phout + ((unsigned)yc * nxu + (unsigned)xq));
+            msum += ((double)q.x + (double)q.y) + ((double)q.z + (double)q.w);
+        }
+    }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) msum += __shfl_down_sync(0xffffffffu, msum, off);
     if (lane == 0) sm.red[wid] = msum;

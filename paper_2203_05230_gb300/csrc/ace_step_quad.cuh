@@ -7,7 +7,9 @@
 // column beside the warp's strip); each warp marches its own strip with a private psi
 // ring and two halo columns under __syncwarp; the pulled populations of the row that
 // collides next are parked in shared memory; 3 CTAs of 128 threads per SM; the row loop
-// is not unrolled; the FP64 mass partial of phi(t) is summed exactly in FP32 parts.
+// is not unrolled; the FP64 mass partial of phi(t) is summed in FP32 parts whose
+// rounded part is an exact integer sum (split_add2i, nothing to flush inside the row
+// loop: a counter-tested FP64 flush there was predicated into every iteration).
 // Every node gets the same arithmetic on the same values as in the other FP32 kernels
 // (collide_core, phi summed over planes 0..8 in order), so the states are bit-identical.
 //
@@ -16,7 +18,8 @@
 // are 6 rows tall and spend a quarter of their work on the two psi rows recomputed at
 // each band edge and on filling and draining the row pipeline.
 //
-// Requirement (checked by the host): nx a multiple of 4.
+// Requirements (checked by the host): nx a multiple of 4; at most 4095 rows per CTA
+// (the integer part of the mass partial is exact for up to 4 x 4095 values below 2).
 #pragma once
 
 #include "ace_kernels.cuh"
@@ -120,9 +123,9 @@ __device__ __forceinline__ void quad32_tile(const StepArgs<float>& a, const Vel&
     };
 
     float4 php = make_float4(0.0f, 0.0f, 0.0f, 0.0f); // phi(t) of the row that collides next
-    float2 mhi = make_float2(0.0f, 0.0f), mlo = make_float2(0.0f, 0.0f);
-    double md = 0.0;
-    int mrows = 0;
+    float2 mlo = make_float2(0.0f, 0.0f);
+    unsigned mai = 0u;
+    float mmax = 0.0f;
 
     auto body = [&](int k) {
         // columns beside the quad of the x-shifted planes, from the neighbouring lanes
@@ -224,12 +227,9 @@ __device__ __forceinline__ void quad32_tile(const StepArgs<float>& a, const Vel&
                     *reinterpret_cast<float4*>(a.fout + (o + (unsigned)i * plane)) =
                         make_float4(o2[0][i].x, o2[0][i].y, o2[1][i].x, o2[1][i].y);
                 *reinterpret_cast<float4*>(a.phi + o) = php;
-                split_add2(mhi, mlo, make_float2(php.x, php.y));
-                split_add2(mhi, mlo, make_float2(php.z, php.w));
-                if (++mrows == 64) { // keep the exact FP32 sum of multiples of 2^-16 below 256
-                    md += split_flush(mhi, mlo);
-                    mrows = 0;
-                }
+                split_add2i(mai, mlo, make_float2(php.x, php.y));
+                split_add2i(mai, mlo, make_float2(php.z, php.w));
+                mmax = fmaxf(mmax, fmaxf(fmaxf(fabsf(php.x), fabsf(php.y)), fmaxf(fabsf(php.z), fabsf(php.w))));
             }
         }
         php = make_float4(s0.x, s0.y, s1.x, s1.y);
@@ -241,7 +241,16 @@ __device__ __forceinline__ void quad32_tile(const StepArgs<float>& a, const Vel&
         for (int k = 0; k < nk; ++k) body(k);
     }
 
-    double msum = md + split_flush(mhi, mlo);
+    double msum;
+    if (mmax < 2.0f) {
+        msum = split_total_i(mai, mlo, live && act ? 4u * (unsigned)(y1 - y0) : 0u);
+    } else { // a value of 2 or more: the FP64 sum of the phi this thread wrote
+        msum = 0.0;
+        for (int yc = y0; yc < y1; ++yc) {
+            const float4 q = *reinterpret_cast<const float4*>(a.phi + ((unsigned)yc * nxu + (unsigned)xq));
+            msum += ((double)q.x + (double)q.y) + ((double)q.z + (double)q.w);
+        }
+    }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) msum += __shfl_down_sync(0xffffffffu, msum, off);
     if (lane == 0) sm.red[wid] = msum;

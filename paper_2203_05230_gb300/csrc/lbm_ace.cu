@@ -5,6 +5,7 @@
 // and issues one fused step kernel per time step on the caller's stream.
 #include "lbm_ace.h"
 #include "ace_kernels.cuh"
+#include "ace_reduce.cuh"
 #include "ace_step_bulk.cuh"
 #include "ace_step_warp.cuh"
 #include "ace_step_pair.cuh"
@@ -15,6 +16,7 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -63,7 +65,8 @@ struct lbm_ace_ctx {
     double* step_part = nullptr; int n_step_part = 0;
     double* red_part = nullptr; int n_red_part = 0;
     double* result = nullptr;
-    double* hres = nullptr; // pinned host copy of the result block (small, fast read-back)
+    double* hres = nullptr;     // mapped pinned host block the finishing kernels write results to
+    double* hres_dev = nullptr; // its device address
     double* scratch = nullptr; size_t scratch_elems = 0; // FP64 staging for state/phi copies
     VelState vel;
     long long t = 0;
@@ -241,9 +244,14 @@ void launch_dev_k(lbm_ace_ctx* c, const Vel& vel)
 {
     dim3 grid(c->grid_x, c->grid_y);
     StepArgs<float> a = make_args<float>(c);
-    if (c->variant == 7 && c->dev4_ctas == 4)
-        launch_pdl_smem(ace_step_dev4<S, MODEL, Vel, 4>, grid, QUAD_THREADS, c->smem, c->stream, make_dev<S>(c), a, vel);
-    else if (c->variant == 7)
+    if constexpr (Vel::row_uniform) { // the 4-CTA instantiation exists for these velocities only
+        if (c->variant == 7 && c->dev4_ctas == 4) {
+            launch_pdl_smem(ace_step_dev4<S, MODEL, Vel, 4>, grid, QUAD_THREADS, c->smem, c->stream, make_dev<S>(c), a,
+                            vel);
+            return;
+        }
+    }
+    if (c->variant == 7)
         launch_pdl_smem(ace_step_dev4<S, MODEL, Vel, 3>, grid, QUAD_THREADS, c->smem, c->stream, make_dev<S>(c), a, vel);
     else
         launch_pdl(ace_step_dev<S, MODEL, Vel>, grid, PAIR_THREADS, c->stream, make_dev<S>(c), a, vel);
@@ -455,9 +463,13 @@ template <typename S, int MODEL, class Vel>
 int occupancy_dev_k(lbm_ace_ctx* c, int* blocks)
 {
     if (c->variant == 7) {
-        // 4 CTAs/SM above 2^23 nodes (measured faster at 4096^2), 3 below (faster at 2048^2)
-        c->dev4_ctas = (long long)c->p.nx * c->p.ny > (1LL << 23) ? 4 : 3;
-        auto k = c->dev4_ctas == 4 ? ace_step_dev4<S, MODEL, Vel, 4> : ace_step_dev4<S, MODEL, Vel, 3>;
+        // 4 CTAs/SM above 2^23 nodes (measured faster at 4096^2), 3 below (faster at 2048^2);
+        // velocity planes (per-node loads) always 3: at the 128-register cap of 4 CTAs/SM
+        // that instantiation spills
+        c->dev4_ctas = Vel::row_uniform && (long long)c->p.nx * c->p.ny > (1LL << 23) ? 4 : 3;
+        auto k = ace_step_dev4<S, MODEL, Vel, 3>;
+        if constexpr (Vel::row_uniform)
+            if (c->dev4_ctas == 4) k = ace_step_dev4<S, MODEL, Vel, 4>;
         c->smem = sizeof(QuadSmem);
         c->tile_x = QUAD_COLS;
         CK(c, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c->smem));
@@ -523,16 +535,14 @@ int callback_upload(lbm_ace_ctx* c, double t, int pair)
 
 int check_device_error(lbm_ace_ctx* c);
 
-// The sum in the result block and the wait-failure flag right after it, in one copy.
+// The sum and the wait-failure flag, which the finishing kernel wrote to the mapped host
+// block (write_result): no copy, only the stream synchronisation.
 int fetch_result(lbm_ace_ctx* c, double* out)
 {
     CK(c, cudaGetLastError());
-    double* back = c->hres;
-    CK(c, cudaMemcpyAsync(back, c->result, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
-    int e;
-    std::memcpy(&e, &back[2], sizeof e);
-    if (e) {
+    const double* back = c->hres;
+    if (back[1] != 0.0) {
         CK(c, cudaMemsetAsync(c->dev_err, 0, sizeof(int), c->stream));
         CK(c, cudaStreamSynchronize(c->stream));
         return fail(c, LBM_ACE_ETIMEOUT, "a bounded wait in the step kernel gave up; the state is not valid");
@@ -543,7 +553,7 @@ int fetch_result(lbm_ace_ctx* c, double* out)
 
 int finalize_sum(lbm_ace_ctx* c, const double* part, int n, double* out)
 {
-    ace_finalize<<<1, RED_THREADS, 0, c->stream>>>(part, n, c->result);
+    ace_finalize<<<1, RED_THREADS, 0, c->stream>>>(part, n, c->hres_dev, c->dev_err);
     return fetch_result(c, out);
 }
 
@@ -724,7 +734,9 @@ static int init_impl(lbm_ace_ctx* c, const lbm_ace_params* p)
     c->dev_err = reinterpret_cast<int*>(c->result + 2);
 
     CK(c, cudaMemset(c->result, 0, 4 * sizeof(double)));
-    CK(c, cudaMallocHost(&c->hres, 4 * sizeof(double)));
+    CK(c, cudaHostAlloc(&c->hres, 4 * sizeof(double), cudaHostAllocMapped));
+    CK(c, cudaHostGetDevicePointer(&c->hres_dev, c->hres, 0));
+    std::memset(c->hres, 0, 4 * sizeof(double));
 
     // kernel variant, automatic choice measured on GB300 (FP32): four columns per thread in warp strips
     // up to 2^23 nodes (1024^2: 71k against 67k MLUPS for column pairs; 2048^2: 80k against
@@ -762,11 +774,35 @@ static int init_impl(lbm_ace_ctx* c, const lbm_ace_params* p)
         rows = (int)r;
     }
     if (rows > ny) rows = ny;
+    // the integer part of the quad kernels' mass partials is exact for bands of at most
+    // 4095 rows (four values below 2 per thread and row)
+    const int max_rows = (c->variant == 7 || c->variant == 8) ? 4095 : ny;
+    if (rows > max_rows) {
+        if (p->rows_per_cta > 0)
+            return fail(c, LBM_ACE_EINVAL, "rows_per_cta %d: kernel variant %d takes at most %d rows per CTA",
+                        p->rows_per_cta, c->variant, max_rows);
+        rows = max_rows;
+    }
     c->rows = rows;
     c->grid_y = (ny + rows - 1) / rows;
     c->n_step_part = c->grid_x * c->grid_y;
     CK(c, cudaMalloc(&c->step_part, c->n_step_part * sizeof(double)));
-    c->n_red_part = grid_for(9 * (long long)n, c->sms);
+    // global mass: FP64 states by the compensated grid-stride kernel, the others by the
+    // fused kernels sized to one wave of resident CTAs (FP32: 4 CTAs/SM of the 6 that
+    // fit, measured 35.0 against 36.9 us at 2048^2; 16-bit: all that fit)
+    {
+        int rocc = 0;
+        if (p->precision == LBM_ACE_F32) {
+            CK(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&rocc, ace_sum_partials_f32, RED_THREADS, 0));
+            rocc = std::min(rocc, 4);
+        }
+        else if (p->precision == LBM_ACE_F16DEV)
+            CK(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&rocc, ace_sum_partials_dev<__half>, RED_THREADS, 0));
+        else if (p->precision == LBM_ACE_BF16DEV)
+            CK(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&rocc, ace_sum_partials_dev<__nv_bfloat16>, RED_THREADS, 0));
+        c->n_red_part = p->precision == LBM_ACE_F64 ? grid_for(9 * (long long)n, c->sms)
+                                                    : mass_reduction_grid(c->sms, rocc, 10 * (long long)n);
+    }
     CK(c, cudaMalloc(&c->red_part, c->n_red_part * sizeof(double)));
 
     // velocity
@@ -1065,17 +1101,18 @@ int lbm_ace_mass(lbm_ace_ctx* c, double* out)
         break;
     case LBM_ACE_F32:
         ace_sum_partials_f32<<<c->n_red_part, RED_THREADS, 0, c->stream>>>((const float*)c->f[c->cur], n9, c->red_part,
-                                                                           done, c->result);
+                                                                           done, c->hres_dev, c->dev_err);
         rc = fetch_result(c, out);
         break;
     case LBM_ACE_F16DEV:
         ace_sum_partials_dev<__half><<<c->n_red_part, RED_THREADS, 0, c->stream>>>(gs, c->phi2[c->pcur], n, c->red_part,
-                                                                                   done, c->result);
+                                                                                   done, c->hres_dev, c->dev_err);
         rc = fetch_result(c, out);
         break;
     default:
         ace_sum_partials_dev<__nv_bfloat16><<<c->n_red_part, RED_THREADS, 0, c->stream>>>(gs, c->phi2[c->pcur], n,
-                                                                                          c->red_part, done, c->result);
+                                                                                          c->red_part, done, c->hres_dev,
+                                                                                          c->dev_err);
         rc = fetch_result(c, out);
         break;
     }

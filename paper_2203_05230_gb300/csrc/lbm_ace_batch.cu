@@ -20,6 +20,7 @@
 // kernel stops pulling work there. Retired lattices cost nothing, in the graph too.
 #include "lbm_ace.h"
 #include "ace_kernels.cuh"
+#include "ace_reduce.cuh"
 #include "ace_step_pair.cuh"
 
 #include <cuda_runtime.h>
@@ -441,11 +442,14 @@ int lbm_ace_batch_init(const lbm_ace_params* params, int count, lbm_ace_batch** 
     BI(cudaMalloc(&b->phase, count * sizeof(float2)));
     BI(cudaMalloc(&b->d_end_sorted, count * sizeof(long long)));
     BI(cudaMalloc(&b->d_prefix, count * sizeof(int)));
-    BI(cudaMalloc(&b->result, 2 * sizeof(double))); // the mass, then the reduction's ticket counter
-    BI(cudaMemset(b->result, 0, 2 * sizeof(double)));
+    // the mass and the flag slot of write_result, a spare, the reduction's ticket counter
+    BI(cudaMalloc(&b->result, 4 * sizeof(double)));
+    BI(cudaMemset(b->result, 0, 4 * sizeof(double)));
     long long maxn = 0;
     for (const auto& q : b->p) maxn = std::max(maxn, (long long)q.nx * q.ny);
-    b->n_red = (int)std::min<long long>((9 * maxn + 255) / 256, (long long)b->sms * 8);
+    int rocc = 0;
+    BI(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&rocc, ace_sum_partials_f32, RED_THREADS, 0));
+    b->n_red = mass_reduction_grid(b->sms, std::min(rocc, 4), 9 * maxn); // as the single-lattice library
     BI(cudaMalloc(&b->red_part, b->n_red * sizeof(double)));
 
     b->inst.resize(count);
@@ -734,7 +738,8 @@ int lbm_ace_batch_mass(lbm_ace_batch* b, int i, double* out)
     const BatchInst& I = b->inst[i];
     const long long n9 = 9LL * I.nx * I.ny;
     ace_sum_partials_f32<<<b->n_red, RED_THREADS, 0, b->stream>>>(I.f[std::min(b->t, I.end) & 1], n9, b->red_part,
-                                                                  reinterpret_cast<unsigned*>(b->result + 1), b->result);
+                                                                  reinterpret_cast<unsigned*>(b->result + 3), b->result,
+                                                                  nullptr);
     BK(b, cudaGetLastError());
     BK(b, cudaMemcpyAsync(out, b->result, sizeof(double), cudaMemcpyDeviceToHost, b->stream));
     BK(b, cudaStreamSynchronize(b->stream));
