@@ -4,6 +4,7 @@
 // plane, velocity tables or planes, reduction partials), validates parameters,
 // and issues one fused step kernel per time step on the caller's stream.
 #include "lbm_ace.h"
+#include "ctx_id.h"
 #include "ace_kernels.cuh"
 #include "ace_reduce.cuh"
 #include "ace_step_bulk.cuh"
@@ -21,6 +22,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <utility>
@@ -37,6 +39,91 @@ constexpr double kPi = 3.14159265358979323846;
 // before any device work; larger ones right after their upload, on the device (a host
 // pass over a 2048^2 field costs milliseconds)
 constexpr size_t kHostCheckMax = 1u << 16;
+
+// --- memory of the contexts ----------------------------------------------------------
+// Device buffers come from one stream-ordered memory pool per device that keeps the
+// blocks a destroyed context frees (no release threshold), so a lattice created after
+// another one was destroyed reuses that memory. Measured on GB300: the six buffers of a
+// 2048^2 FP32 lattice cost 225 us through cudaMalloc, 7 us from the pool.
+// lbm_ace_release_cached_memory hands the unused blocks back to the driver. A pool lives
+// as long as the device's context: after cudaDeviceReset (a new context id) a new one
+// is made. The calls below run with `dev` current.
+constexpr int kMaxDevices = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pools[kMaxDevices] = {};
+unsigned long long g_pool_ctx[kMaxDevices] = {};
+
+cudaError_t device_pool(int dev, cudaMemPool_t* out)
+{
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    unsigned long long id = 0;
+    if (!current_ctx_id(&id)) return cudaErrorDeviceUninitialized;
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    if (!g_pools[dev] || g_pool_ctx[dev] != id) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t pool;
+        cudaError_t e = cudaMemPoolCreate(&pool, &props);
+        if (e != cudaSuccess) return e;
+        unsigned long long keep = ~0ULL;
+        e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        if (e != cudaSuccess) {
+            cudaMemPoolDestroy(pool);
+            return e;
+        }
+        g_pools[dev] = pool;
+        g_pool_ctx[dev] = id;
+    }
+    *out = g_pools[dev];
+    return cudaSuccess;
+}
+
+// Mapped pinned host memory for the contexts' result blocks, in 128-byte slots (one
+// cache line each) cut from 4 KiB pages that are never freed: a cudaHostAlloc costs
+// about 80 us, more than a whole mass call. A page belongs to the CUDA context that was
+// current when it was allocated and dies with it (cudaDeviceReset), so every slot
+// carries that context's id and is handed out only while the same context is current.
+struct PinnedSlot { double* host; double* dev; unsigned long long ctx; };
+std::mutex g_slot_mu;
+std::vector<PinnedSlot> g_free_slots;
+constexpr size_t kSlotBytes = 128, kSlotPage = 4096;
+
+cudaError_t acquire_slot(PinnedSlot* out)
+{
+    unsigned long long id = 0;
+    if (!current_ctx_id(&id)) return cudaErrorDeviceUninitialized;
+    std::lock_guard<std::mutex> lock(g_slot_mu);
+    for (size_t k = g_free_slots.size(); k-- > 0;)
+        if (g_free_slots[k].ctx == id) {
+            *out = g_free_slots[k];
+            g_free_slots.erase(g_free_slots.begin() + (long)k);
+            std::memset(out->host, 0, kSlotBytes);
+            return cudaSuccess;
+        }
+    void* page = nullptr;
+    cudaError_t e = cudaHostAlloc(&page, kSlotPage, cudaHostAllocMapped | cudaHostAllocPortable);
+    if (e != cudaSuccess) return e;
+    void* dpage = nullptr;
+    e = cudaHostGetDevicePointer(&dpage, page, 0);
+    if (e != cudaSuccess) {
+        cudaFreeHost(page);
+        return e;
+    }
+    for (size_t off = kSlotBytes; off < kSlotPage; off += kSlotBytes) // slot 0 is handed out now
+        g_free_slots.push_back({reinterpret_cast<double*>(static_cast<char*>(page) + off),
+                                reinterpret_cast<double*>(static_cast<char*>(dpage) + off), id});
+    *out = {static_cast<double*>(page), static_cast<double*>(dpage), id};
+    std::memset(out->host, 0, kSlotBytes);
+    return cudaSuccess;
+}
+
+void release_slot(const PinnedSlot& s)
+{
+    std::lock_guard<std::mutex> lock(g_slot_mu);
+    g_free_slots.push_back(s);
+}
 
 struct VelState {
     // single vortex tables, in the storage precision of the arithmetic (T)
@@ -65,7 +152,8 @@ struct lbm_ace_ctx {
     double* step_part = nullptr; int n_step_part = 0;
     double* red_part = nullptr; int n_red_part = 0;
     double* result = nullptr;
-    double* hres = nullptr;     // mapped pinned host block the finishing kernels write results to
+    PinnedSlot slot{nullptr, nullptr, 0}; // mapped pinned result block (acquire_slot)
+    double* hres = nullptr;     // its host address: the finishing kernels write results here
     double* hres_dev = nullptr; // its device address
     double* scratch = nullptr; size_t scratch_elems = 0; // FP64 staging for state/phi copies
     VelState vel;
@@ -100,6 +188,26 @@ int fail(lbm_ace_ctx* c, int code, const char* fmt, ...)
         if (e_ != cudaSuccess)                                                                \
             return fail((ctx), e_ == cudaErrorMemoryAllocation ? LBM_ACE_ENOMEM : LBM_ACE_ECUDA, \
                         "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__);  \
+    } while (0)
+
+// A device buffer of the context from the device's pool (device_pool), ready for use on
+// any stream when this returns (the allocation is ordered on the context's stream, which
+// is then synchronised: reused blocks may come from another context's stream).
+template <typename P>
+int pool_alloc(lbm_ace_ctx* c, P** ptr, size_t bytes)
+{
+    cudaMemPool_t pool;
+    CK(c, device_pool(c->dev, &pool));
+    void* q = nullptr;
+    CK(c, cudaMallocFromPoolAsync(&q, bytes, pool, c->stream));
+    *ptr = static_cast<P*>(q);
+    CK(c, cudaStreamSynchronize(c->stream));
+    return LBM_ACE_OK;
+}
+#define PA(ctx, ptr, bytes)                              \
+    do {                                                 \
+        const int rc_ = pool_alloc((ctx), (ptr), (bytes)); \
+        if (rc_) return rc_;                             \
     } while (0)
 
 int grid_for(long long n, int sms) // grid of a grid-stride elementwise kernel
@@ -391,10 +499,10 @@ int fill_vortex_tables(lbm_ace_ctx* c)
         sy2[y] = T(s * s);
         s2y[y] = T(std::sin(2.0 * kPi * y / ny));
     }
-    CK(c, cudaMalloc(&c->vel.sx2, nx * sizeof(T)));
-    CK(c, cudaMalloc(&c->vel.s2x, nx * sizeof(T)));
-    CK(c, cudaMalloc(&c->vel.sy2, ny * sizeof(T)));
-    CK(c, cudaMalloc(&c->vel.s2y, ny * sizeof(T)));
+    PA(c, &c->vel.sx2, nx * sizeof(T));
+    PA(c, &c->vel.s2x, nx * sizeof(T));
+    PA(c, &c->vel.sy2, ny * sizeof(T));
+    PA(c, &c->vel.s2y, ny * sizeof(T));
     CK(c, cudaMemcpy(c->vel.sx2, sx2.data(), nx * sizeof(T), cudaMemcpyHostToDevice));
     CK(c, cudaMemcpy(c->vel.s2x, s2x.data(), nx * sizeof(T), cudaMemcpyHostToDevice));
     CK(c, cudaMemcpy(c->vel.sy2, sy2.data(), ny * sizeof(T), cudaMemcpyHostToDevice));
@@ -512,10 +620,10 @@ bool is_dev(const lbm_ace_ctx* c) { return c->p.precision == LBM_ACE_F16DEV || c
 int ensure_scratch(lbm_ace_ctx* c, size_t elems)
 {
     if (c->scratch_elems >= elems) return LBM_ACE_OK;
-    if (c->scratch) cudaFree(c->scratch);
+    if (c->scratch) cudaFreeAsync(c->scratch, c->stream);
     c->scratch = nullptr;
     c->scratch_elems = 0;
-    CK(c, cudaMalloc(&c->scratch, elems * sizeof(double)));
+    PA(c, &c->scratch, elems * sizeof(double));
     c->scratch_elems = elems;
     return LBM_ACE_OK;
 }
@@ -702,8 +810,8 @@ void lbm_ace_destroy(lbm_ace_ctx* c)
                     c->scratch,
                     c->vel.sx2, c->vel.s2x, c->vel.sy2, c->vel.s2y,
                     c->vel.pu[0], c->vel.pu[1], c->vel.pv[0], c->vel.pv[1]};
-    for (void* b : bufs) if (b) cudaFree(b);
-    if (c->hres) cudaFreeHost(c->hres);
+    for (void* b : bufs) if (b) cudaFreeAsync(b, c->stream); // back to the device's pool
+    if (c->slot.host) release_slot(c->slot);
     delete c;
 }
 
@@ -719,24 +827,24 @@ static int init_impl(lbm_ace_ctx* c, const lbm_ace_params* p)
     const size_t n = (size_t)nx * ny;
     c->elem = is_f64(c) ? sizeof(double) : (is_dev(c) ? 2 : sizeof(float));
 
-    CK(c, cudaMalloc(&c->f[0], 9 * n * c->elem));
-    CK(c, cudaMalloc(&c->f[1], 9 * n * c->elem));
+    PA(c, &c->f[0], 9 * n * c->elem);
+    PA(c, &c->f[1], 9 * n * c->elem);
     if (is_dev(c)) {
-        CK(c, cudaMalloc(&c->phi2[0], n * sizeof(float)));
-        CK(c, cudaMalloc(&c->phi2[1], n * sizeof(float)));
+        PA(c, &c->phi2[0], n * sizeof(float));
+        PA(c, &c->phi2[1], n * sizeof(float));
     } else {
-        CK(c, cudaMalloc(&c->phi, n * c->elem));
+        PA(c, &c->phi, n * c->elem);
     }
-    if (p->kernel_variant == 6) CK(c, cudaMalloc(&c->phi_alt, n * sizeof(float)));
+    if (p->kernel_variant == 6) PA(c, &c->phi_alt, n * sizeof(float));
     // result block: the reduced sum, a spare double, the device wait-failure flag, and the
     // ticket counter of the mass reductions that finish in their last CTA
-    CK(c, cudaMalloc(&c->result, 4 * sizeof(double)));
+    PA(c, &c->result, 4 * sizeof(double));
     c->dev_err = reinterpret_cast<int*>(c->result + 2);
 
-    CK(c, cudaMemset(c->result, 0, 4 * sizeof(double)));
-    CK(c, cudaHostAlloc(&c->hres, 4 * sizeof(double), cudaHostAllocMapped));
-    CK(c, cudaHostGetDevicePointer(&c->hres_dev, c->hres, 0));
-    std::memset(c->hres, 0, 4 * sizeof(double));
+    CK(c, cudaMemsetAsync(c->result, 0, 4 * sizeof(double), c->stream));
+    CK(c, acquire_slot(&c->slot));
+    c->hres = c->slot.host;
+    c->hres_dev = c->slot.dev;
 
     // kernel variant, automatic choice measured on GB300 (FP32): four columns per thread in warp strips
     // up to 2^23 nodes (1024^2: 71k against 67k MLUPS for column pairs; 2048^2: 80k against
@@ -786,7 +894,7 @@ static int init_impl(lbm_ace_ctx* c, const lbm_ace_params* p)
     c->rows = rows;
     c->grid_y = (ny + rows - 1) / rows;
     c->n_step_part = c->grid_x * c->grid_y;
-    CK(c, cudaMalloc(&c->step_part, c->n_step_part * sizeof(double)));
+    PA(c, &c->step_part, c->n_step_part * sizeof(double));
     // global mass: FP64 states by the compensated grid-stride kernel, the others by the
     // fused kernels sized to one wave of resident CTAs (FP32: 4 CTAs/SM of the 6 that
     // fit, measured 35.0 against 36.9 us at 2048^2; 16-bit: all that fit)
@@ -803,7 +911,7 @@ static int init_impl(lbm_ace_ctx* c, const lbm_ace_params* p)
         c->n_red_part = p->precision == LBM_ACE_F64 ? grid_for(9 * (long long)n, c->sms)
                                                     : mass_reduction_grid(c->sms, rocc, 10 * (long long)n);
     }
-    CK(c, cudaMalloc(&c->red_part, c->n_red_part * sizeof(double)));
+    PA(c, &c->red_part, c->n_red_part * sizeof(double));
 
     // velocity
     if (p->velocity_kind == LBM_ACE_VEL_SINGLE_VORTEX) {
@@ -812,8 +920,8 @@ static int init_impl(lbm_ace_ctx* c, const lbm_ace_params* p)
     } else if (p->velocity_kind == LBM_ACE_VEL_FIELD || p->velocity_kind == LBM_ACE_VEL_CALLBACK) {
         const int pairs = p->velocity_kind == LBM_ACE_VEL_CALLBACK ? 2 : 1;
         for (int k = 0; k < pairs; ++k) {
-            CK(c, cudaMalloc(&c->vel.pu[k], n * sizeof(double)));
-            CK(c, cudaMalloc(&c->vel.pv[k], n * sizeof(double)));
+            PA(c, &c->vel.pu[k], n * sizeof(double));
+            PA(c, &c->vel.pv[k], n * sizeof(double));
         }
         if (pairs == 1) {
             CK(c, cudaMemcpy(c->vel.pu[0], p->u_field, n * sizeof(double), cudaMemcpyHostToDevice));
@@ -1076,6 +1184,24 @@ int lbm_ace_reset_device(lbm_ace_ctx* c, const float* phi, long long t)
 }
 
 void* lbm_ace_get_stream(const lbm_ace_ctx* c) { return c ? (void*)c->stream : nullptr; }
+
+int lbm_ace_release_cached_memory(int device)
+{
+    if (device < 0 || device >= kMaxDevices) return fail(nullptr, LBM_ACE_EINVAL, "device %d out of range", device);
+    DeviceGuard g(device);
+    unsigned long long id = 0;
+    cudaMemPool_t pool = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_pool_mu);
+        if (current_ctx_id(&id) && g_pool_ctx[device] == id) pool = g_pools[device];
+    }
+    if (!pool) return LBM_ACE_OK; // nothing allocated in the device's current context
+    // the frees of destroyed contexts are ordered on their streams: let them land first
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemPoolTrimTo(pool, 0);
+    if (e != cudaSuccess) return fail(nullptr, LBM_ACE_ECUDA, "releasing cached memory: %s", cudaGetErrorString(e));
+    return LBM_ACE_OK;
+}
 
 int lbm_ace_get_params(const lbm_ace_ctx* c, lbm_ace_params* out)
 {

@@ -13,6 +13,7 @@
 // loads the library, for as long as the library stays loaded. The entry point calls
 // no cudaMalloc, cudaFree or other allocating routine.
 #include "lbm_ace.h"
+#include "ctx_id.h"
 
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -70,36 +71,6 @@ __global__ void mass_partials_final(const double* __restrict__ partials, int n, 
     if (lane == 0) *out = S + C;
 }
 
-// Identity of the calling thread's current CUDA context (cuCtxGetId: unique for the
-// life of the process, so a context created after cudaDeviceReset gets a new one).
-// The two driver functions come through the runtime, so the library does not link
-// the driver library itself.
-using CtxGetCurrentFn = CUresult (*)(CUcontext*);
-using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
-
-CtxGetCurrentFn g_get_cur = nullptr;
-CtxGetIdFn g_get_id = nullptr;
-std::once_flag g_fn_once;
-
-bool current_ctx_id(unsigned long long* id)
-{
-    std::call_once(g_fn_once, [] {
-        void* f1 = nullptr;
-        void* f2 = nullptr;
-        cudaDriverEntryPointQueryResult q1 = cudaDriverEntryPointSymbolNotFound, q2 = q1;
-        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
-            cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
-            q1 == cudaDriverEntryPointSuccess && q2 == cudaDriverEntryPointSuccess) {
-            g_get_cur = reinterpret_cast<CtxGetCurrentFn>(f1);
-            g_get_id = reinterpret_cast<CtxGetIdFn>(f2);
-        }
-    });
-    if (!g_get_cur || !g_get_id) return false;
-    CUcontext ctx = nullptr;
-    if (g_get_cur(&ctx) != CUDA_SUCCESS || !ctx) return false;
-    return g_get_id(ctx, id) == CUDA_SUCCESS;
-}
-
 // Device address of the scratch array for the current device. In host code the
 // array's name is only a host-side stand-in, so the address is looked up
 // (cudaGetSymbolAddress, with the device current) at the first call on a device and
@@ -112,7 +83,7 @@ unsigned long long g_ctx[kMaxDevices] = {};
 cudaError_t scratch_for(int dev, double** out)
 {
     unsigned long long id = 0;
-    if (!current_ctx_id(&id)) return cudaErrorDeviceUninitialized;
+    if (!lbmace::current_ctx_id(&id)) return cudaErrorDeviceUninitialized;
     std::lock_guard<std::mutex> lock(g_mu);
     if (!g_ptr[dev] || g_ctx[dev] != id) {
         void* p = nullptr;

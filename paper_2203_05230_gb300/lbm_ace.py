@@ -46,7 +46,7 @@ EXPORTS = (
     "lbm_ace_batch_step_per_lattice", "lbm_ace_batch_set_ends", "lbm_ace_batch_lattice_steps",
     "lbm_ace_batch_active",
     "lbm_ace_get_phi_device", "lbm_ace_velocity_device", "lbm_ace_reset_device", "lbm_ace_get_stream",
-    "lbm_ace_get_params", "lbm_ace_wait_selftest",
+    "lbm_ace_get_params", "lbm_ace_wait_selftest", "lbm_ace_release_cached_memory",
     "lbm_ace_net_create", "lbm_ace_net_set_params", "lbm_ace_net_get_params", "lbm_ace_net_forward",
     "lbm_ace_net_loss_grad", "lbm_ace_net_adam", "lbm_ace_net_gather", "lbm_ace_net_metrics",
     "lbm_ace_net_synchronize", "lbm_ace_net_last_error", "lbm_ace_net_destroy", "lbm_ace_hybrid_advance",
@@ -120,6 +120,7 @@ def load(build_if_missing: bool = True):
     L.lbm_ace_launch_shape.argtypes = [_P] + [ctypes.POINTER(ctypes.c_int)] * 5
     L.lbm_ace_synchronize.argtypes = [_P]
     L.lbm_ace_wait_selftest.argtypes = [_P, ctypes.c_longlong]
+    L.lbm_ace_release_cached_memory.argtypes = [ctypes.c_int]
     L.lbm_ace_last_error.argtypes = [_P]
     L.lbm_ace_last_error.restype = ctypes.c_char_p
     L.lbm_ace_status_string.argtypes = [ctypes.c_int]
@@ -609,6 +610,12 @@ def lbm_ace_mass_noalloc(values_ptr: int, precision: int, count: int, out_ptr: i
     static device array, so overlapping calls on the GPU race (see include/lbm_ace.h)."""
     return int(load().lbm_ace_mass_noalloc(_P(values_ptr), int(precision), int(count),
                                            _P(out_ptr), _P(int(getattr(stream, "cuda_stream", stream)))))
+
+
+def release_cached_memory(device: int = 0) -> None:
+    """Hand the device memory that destroyed lattices left in the library's pool back to
+    the driver (lbm_ace_release_cached_memory); live lattices keep theirs."""
+    _check(None, load().lbm_ace_release_cached_memory(int(device)))
 
 
 def status_string(rc: int) -> str:
