@@ -250,8 +250,9 @@ int lbm_ace_get_params(const lbm_ace_ctx* c, lbm_ace_params* out);
  * Each lattice of a batch is a single-vortex problem (Section 3, Eq. 14) with its own
  * size, disk, eps, tau, U0 and period, FP32 populations, and one model for the whole
  * batch. A batch step advances every lattice by one time step with one launch of a
- * persistent kernel (one CTA per resident slot pulling tiles of all lattices from a
- * work counter), replayed from a captured CUDA graph; the time t is shared. The
+ * persistent kernel (resident CTAs whose warps, or whole CTAs, pull work items of all
+ * lattices from a work counter), replayed from a captured CUDA graph; the time t is
+ * shared. The
  * batch owns its device memory and works on params[0].stream (or on a stream of its
  * own when that is NULL, since graphs cannot be captured on the legacy stream). */
 typedef struct lbm_ace_batch lbm_ace_batch;
@@ -259,8 +260,11 @@ typedef struct lbm_ace_batch lbm_ace_batch;
 /* Build a batch of `count` lattices from params[0..count-1]. Each needs precision
  * LBM_ACE_F32, velocity LBM_ACE_VEL_SINGLE_VORTEX, an even nx, phi0 == NULL (the disk
  * from xc, yc, R is built on the device), the same model; rows_per_cta sets the tile
- * height of that lattice (0: 64; at least 8 is used). Device and stream come from
- * params[0]. */
+ * height of that lattice (0: 64; at least 8 is used, and at most 4095 with strips).
+ * Work items: when every nx is a multiple of 4, strips of 128 columns, each taken by one
+ * warp with the single-lattice library's four-columns-per-thread code (kernel variant 8);
+ * otherwise tiles of 256 columns, each taken by a CTA with the column-pair code (variant
+ * 4). Device and stream come from params[0]. */
 int lbm_ace_batch_init(const lbm_ace_params* params, int count, lbm_ace_batch** out);
 
 /* Advance the batch's clock by n >= 0 steps: n replays of the captured {step, advance}
@@ -270,9 +274,9 @@ int lbm_ace_batch_init(const lbm_ace_params* params, int count, lbm_ace_batch** 
 int lbm_ace_batch_step(lbm_ace_batch* b, long long n);
 
 /* The same n steps as one ordinary launch per lattice per step (the single-lattice
- * column-pair kernel in the launch shape the single-lattice library picks, host-side
- * loop, lattices past their end skipped): a baseline a batch is compared with.
- * Synchronous. */
+ * kernel of the batch's work-item form -- variant 8 or 4 -- in the launch shape the
+ * single-lattice library picks, host-side loop, lattices past their end skipped): a
+ * baseline a batch is compared with. Synchronous. */
 int lbm_ace_batch_step_sequential(lbm_ace_batch* b, long long n);
 
 /* The same n steps as one launch per lattice per step, all launches of a step captured

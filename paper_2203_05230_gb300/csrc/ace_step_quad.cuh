@@ -39,25 +39,26 @@ struct Quad32Smem {
     double red[Q32_WARPS];
 };
 
+// One warp's work: the strip of columns [x0, x0 + 128) (clipped to nx; none when x0 >= nx)
+// and rows [y0, y1) of the lattice described by `a`, marching up (UP) or down. ring is
+// the warp's psi ring, park the CTA's row buffers (the warp uses the entries of its
+// threads, tx = threadIdx.x). Synchronises the warp only. Returns the FP64 sum of the
+// phi(t) it wrote (every lane holds it).
 template <int MODEL, class Vel, bool UP>
-__device__ __forceinline__ void quad32_tile(const StepArgs<float>& a, const Vel& vel, Quad32Smem& sm)
+__device__ __forceinline__ double quad32_strip(const StepArgs<float>& a, const Vel& vel, int x0, int y0, int y1,
+                                               float (*ring)[Q32_STRIP + 8], float4 (*park_s)[9][Q32_THREADS],
+                                               int tx)
 {
-    const int tx = threadIdx.x;
     const int lane = tx & 31;
-    const int wid = tx >> 5;
-    const int x0 = (blockIdx.x * Q32_WARPS + wid) * Q32_STRIP; // this warp's strip
     const int w = min(Q32_STRIP, a.nx - x0); // a multiple of 4; <= 0 for a strip past the lattice
     const bool live = w > 0;
     const bool act = 4 * lane < w;
     // threads past a ragged edge redo the last quad; a dead strip's threads point at column 0
     const int xq = live ? x0 + (act ? 4 * lane : w - 4) : 0;
-    float (*ring)[Q32_STRIP + 8] = sm.chi[wid];
     const int xl = xq == 0 ? a.nx - 1 : xq - 1;
     const int xr = xq + 4 == a.nx ? 0 : xq + 4;
     const bool own_left = lane == 0;
     const bool own_right = lane == 31 || 4 * (lane + 1) >= w;
-    const int y0 = blockIdx.y * a.rows;
-    const int y1 = min(y0 + a.rows, a.ny);
     const int nk = y1 - y0 + 2;
     const unsigned nxu = (unsigned)a.nx, plane = (unsigned)a.plane;
 
@@ -161,7 +162,7 @@ __device__ __forceinline__ void quad32_tile(const StepArgs<float>& a, const Vel&
             s0 = __fadd2_rn(s0, f[0][i]);
             s1 = __fadd2_rn(s1, f[1][i]);
         }
-        float4* park = sm.park[k & 1][0] + tx;
+        float4* park = park_s[k & 1][0] + tx;
 #pragma unroll
         for (int i = 0; i < 9; ++i) park[i * Q32_THREADS] = make_float4(f[0][i].x, f[0][i].y, f[1][i].x, f[1][i].y);
         if (act) {
@@ -201,7 +202,7 @@ __device__ __forceinline__ void quad32_tile(const StepArgs<float>& a, const Vel&
                 const typename Vel::Row vq = (Vel::row_uniform || q == 0) ? vr : vel.rowv(cq[q], xq + q, yc);
                 vel.at(cq[q], vq, uu[q], vv[q], up[q], vp[q]);
             }
-            const float4* pk = sm.park[(k - 1) & 1][0] + tx;
+            const float4* pk = park_s[(k - 1) & 1][0] + tx;
             const float ph[4] = {php.x, php.y, php.z, php.w};
             const float pp[4] = {ppc.x, ppc.y, ppc.z, ppc.w};
             const unsigned o = (unsigned)yc * nxu + (unsigned)xq;
@@ -252,8 +253,23 @@ __device__ __forceinline__ void quad32_tile(const StepArgs<float>& a, const Vel&
         }
     }
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) msum += __shfl_down_sync(0xffffffffu, msum, off);
-    if (lane == 0) sm.red[wid] = msum;
+    for (int off = 16; off > 0; off >>= 1) msum += __shfl_xor_sync(0xffffffffu, msum, off);
+    return msum;
+}
+
+// One CTA of the single-lattice kernel: warp wid takes strip blockIdx.x * 4 + wid of the
+// row band blockIdx.y (a.rows tall); the warps' mass sums go, in warp order, to the CTA's
+// partial.
+template <int MODEL, class Vel, bool UP>
+__device__ __forceinline__ void quad32_tile(const StepArgs<float>& a, const Vel& vel, Quad32Smem& sm)
+{
+    const int tx = threadIdx.x;
+    const int wid = tx >> 5;
+    const int x0 = (blockIdx.x * Q32_WARPS + wid) * Q32_STRIP; // this warp's strip
+    const int y0 = blockIdx.y * a.rows;
+    const int y1 = min(y0 + a.rows, a.ny);
+    const double msum = quad32_strip<MODEL, Vel, UP>(a, vel, x0, y0, y1, sm.chi[wid], sm.park, tx);
+    if ((tx & 31) == 0) sm.red[wid] = msum;
     __syncthreads();
     if (tx == 0) {
         double s = 0.0;

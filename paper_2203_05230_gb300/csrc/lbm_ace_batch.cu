@@ -2,10 +2,12 @@
 //
 // A batch holds N lattices of possibly different sizes and parameters (each a
 // single-vortex problem of Section 3 / Eq. 14, FP32 populations). One time step of the
-// batch is one launch of a persistent kernel: a grid of (SMs x resident CTAs) CTAs that
-// pull work items -- one tile (256 columns x rows) of one lattice -- from an atomic
-// counter and run the column-pair step (pair_tile, shared with the single-lattice
-// kernel) on each, so small lattices that could never fill the GPU alone share it.
+// batch is one launch of a persistent kernel: a grid of (SMs x resident CTAs) CTAs whose
+// warps (when every nx is a multiple of 4) or CTAs (otherwise) pull work items from an
+// atomic counter -- a 128-column strip or a 256-column tile of one row band of one
+// lattice -- and run the single-lattice kernels' code on each (quad32_strip of the FP32
+// quad kernel, or pair_tile of the column-pair kernel), so small lattices that could
+// never fill the GPU alone share it.
 // The step counter t lives on the device; each lattice's phase cos(pi t / T) is
 // computed there, so a captured graph of {step, advance} replays any number of steps
 // without host work. Tile heights and the persistent grid's CTAs per SM come from
@@ -22,6 +24,7 @@
 #include "ace_kernels.cuh"
 #include "ace_reduce.cuh"
 #include "ace_step_pair.cuh"
+#include "ace_step_quad.cuh"
 
 #include <cuda_runtime.h>
 
@@ -60,11 +63,9 @@ struct BatchCtl {
     int active_next; // the same for time t + 1, filled in by ace_batch_phase
 };
 
-// Tile (bx, by) of lattice I at time t with tiles `rows` tall; the tile's mass partial
-// goes to *mass_out.
-template <int MODEL>
-__device__ __forceinline__ void batch_tile_at(const BatchInst& I, float2 ph, int bx, int by, int rows, int t,
-                                              float (*chi_s)[PAIR_COLS + 4], double* red_s, double* mass_out)
+// Step arguments of lattice I at time t (tiles `rows` tall) and its velocity at the
+// phase ph = (cos(pi t / T), cos(pi (t - 1) / T)).
+__device__ __forceinline__ StepArgs<float> batch_args(const BatchInst& I, int t, int rows)
 {
     StepArgs<float> a;
     a.fin = I.f[t & 1];
@@ -75,16 +76,31 @@ __device__ __forceinline__ void batch_tile_at(const BatchInst& I, float2 ph, int
     a.plane = (long long)I.nx * I.ny;
     a.rows = rows;
     a.first = t == 0;
-    a.tdir = t & 1; // unused by pair_tile's default downward march
+    a.tdir = t & 1;
     a.omega = I.omega; a.fpref = I.fpref;
     a.eps = I.eps; a.inv_eps = I.inv_eps; a.inv4eps = I.inv4eps;
     a.delta = I.delta; a.inv1p2d = I.inv1p2d;
+    return a;
+}
+
+__device__ __forceinline__ VelVortex<float> batch_vel(const BatchInst& I, float2 ph)
+{
     VelVortex<float> vel;
     vel.sx2 = I.sx2; vel.s2x = I.s2x; vel.sy2 = I.sy2; vel.s2y = I.s2y;
     vel.amp = I.amp;
     vel.ct = ph.x;
     vel.ctm1 = ph.y;
-    pair_tile<float, MODEL>(a, vel, bx * PAIR_COLS, by * rows, chi_s, red_s, mass_out);
+    return vel;
+}
+
+// Tile (bx, by) of lattice I at time t with tiles `rows` tall; the tile's mass partial
+// goes to *mass_out. pair_tile marches its default direction (down).
+template <int MODEL>
+__device__ __forceinline__ void batch_tile_at(const BatchInst& I, float2 ph, int bx, int by, int rows, int t,
+                                              float (*chi_s)[PAIR_COLS + 4], double* red_s, double* mass_out)
+{
+    pair_tile<float, MODEL>(batch_args(I, t, rows), batch_vel(I, ph), bx * PAIR_COLS, by * rows, chi_s, red_s,
+                            mass_out);
 }
 
 // Work item lt (row-major over the lattice's tiles of the batch's height I.rows).
@@ -130,6 +146,63 @@ ace_batch_one(const BatchInst* __restrict__ inst, const float2* __restrict__ pha
     if (t < inst[i].end)
         batch_tile_at<MODEL>(inst[i], phase[i], blockIdx.x, blockIdx.y, rows, t, chi_s, red_s,
                              &part[blockIdx.y * gridDim.x + blockIdx.x]);
+}
+
+// The persistent kernel on four-column strips (every lattice's nx a multiple of 4): each
+// warp pulls its own work item -- one 128-column strip of one row band of one lattice --
+// and runs the single-lattice kernel's strip code (quad32_strip) on it, bands marching
+// up or down by band and step parity as in that kernel; the warp's mass sum is the
+// item's partial. Warps of a CTA share nothing but the CTA's shared-memory layout, so a
+// lattice narrower than a CTA's four strips leaves no warp idle.
+template <int MODEL>
+__global__ void __launch_bounds__(Q32_THREADS, Q32_MIN_CTAS)
+ace_batch_step_q(const BatchInst* __restrict__ inst, const float2* __restrict__ phase,
+                 const int* __restrict__ tile_inst, BatchCtl* ctl)
+{
+    extern __shared__ __align__(16) unsigned char bq_smem[];
+    Quad32Smem& sm = *reinterpret_cast<Quad32Smem*>(bq_smem);
+    const int tx = threadIdx.x, lane = tx & 31, wid = tx >> 5;
+    const int t = ctl->t;
+    const int ntiles = ctl->active;
+    for (;;) {
+        int tile = 0;
+        if (lane == 0) tile = atomicAdd(&ctl->next, 1);
+        tile = __shfl_sync(0xffffffffu, tile, 0);
+        if (tile >= ntiles) break;
+        const int i = tile_inst[tile];
+        const BatchInst& I = inst[i];
+        const int lt = tile - I.tile0;
+        const int sx = lt % I.tiles_x, by = lt / I.tiles_x;
+        const StepArgs<float> a = batch_args(I, t, I.rows);
+        const VelVortex<float> vel = batch_vel(I, phase[i]);
+        const int y0 = by * I.rows, y1 = min(y0 + I.rows, I.ny);
+        double m;
+        if (march_up((unsigned)by, a.tdir))
+            m = quad32_strip<MODEL, VelVortex<float>, true>(a, vel, sx * Q32_STRIP, y0, y1, sm.chi[wid], sm.park, tx);
+        else
+            m = quad32_strip<MODEL, VelVortex<float>, false>(a, vel, sx * Q32_STRIP, y0, y1, sm.chi[wid], sm.park, tx);
+        if (lane == 0) I.mass_part[lt] = m;
+    }
+}
+
+// The per-lattice baseline on four-column strips: lattice i alone, in the launch shape of
+// the single-lattice library's quad kernel (CTAs of four strips, bands `rows` tall).
+template <int MODEL>
+__global__ void __launch_bounds__(Q32_THREADS, Q32_MIN_CTAS)
+ace_batch_one_q(const BatchInst* __restrict__ inst, const float2* __restrict__ phase, int i, int rows,
+                const BatchCtl* ctl, double* part)
+{
+    extern __shared__ __align__(16) unsigned char bq_smem[];
+    Quad32Smem& sm = *reinterpret_cast<Quad32Smem*>(bq_smem);
+    const int t = ctl->t;
+    if (t >= inst[i].end) return;
+    StepArgs<float> a = batch_args(inst[i], t, rows);
+    a.mass_part = part;
+    const VelVortex<float> vel = batch_vel(inst[i], phase[i]);
+    if (march_up(blockIdx.y, a.tdir))
+        quad32_tile<MODEL, VelVortex<float>, true>(a, vel, sm);
+    else
+        quad32_tile<MODEL, VelVortex<float>, false>(a, vel, sm);
 }
 
 // For the next step, t + 1: the phase of Eq. 14, (cos(pi (t+1) / T), cos(pi t / T)), per
@@ -187,6 +260,8 @@ struct lbm_ace_batch {
     double* result = nullptr;
     double* scratch = nullptr; size_t scratch_elems = 0;
     int grid = 0, grid_max = 0; // persistent CTAs (tuned), and SMs x resident CTAs
+    bool quad = false;          // every nx a multiple of 4: work items are four-column strips
+    int cols = PAIR_COLS;       // columns of a work item (Q32_STRIP when quad)
     bool own_stream = false;
     long long t = 0;
     cudaGraph_t graph = nullptr;
@@ -238,9 +313,11 @@ int build_tiles(lbm_ace_batch* b)
     for (int j = 0; j < b->n; ++j) {
         const int i = b->order[j];
         BatchInst& I = b->inst[i];
-        // heights below kMinRows would need more mass partials than were allocated
+        // heights below kMinRows would need more mass partials than were allocated; strips
+        // take at most 4095 rows (the exact integer part of their mass sums)
         I.rows = std::max(std::min(kMinRows, I.ny), std::min(I.rows, I.ny));
-        I.tiles_x = (I.nx + PAIR_COLS - 1) / PAIR_COLS;
+        if (b->quad) I.rows = std::min(I.rows, 4095);
+        I.tiles_x = (I.nx + b->cols - 1) / b->cols;
         I.tiles_y = (I.ny + I.rows - 1) / I.rows;
         I.tile0 = (int)b->tile_inst.size();
         for (int k = 0; k < I.tiles_x * I.tiles_y; ++k) b->tile_inst.push_back(i);
@@ -261,7 +338,14 @@ int build_tiles(lbm_ace_batch* b)
 
 void launch_batch_step(lbm_ace_batch* b)
 {
-    if (b->model == LBM_ACE_MODEL_MODIFIED)
+    const size_t qs = sizeof(Quad32Smem);
+    if (b->quad && b->model == LBM_ACE_MODEL_MODIFIED)
+        ace_batch_step_q<MODEL_MODIFIED><<<b->grid, Q32_THREADS, qs, b->stream>>>(b->d_inst, b->phase,
+                                                                                 b->d_tile_inst, b->ctl);
+    else if (b->quad)
+        ace_batch_step_q<MODEL_CONSERVATIVE><<<b->grid, Q32_THREADS, qs, b->stream>>>(b->d_inst, b->phase,
+                                                                                     b->d_tile_inst, b->ctl);
+    else if (b->model == LBM_ACE_MODEL_MODIFIED)
         ace_batch_step<MODEL_MODIFIED><<<b->grid, PAIR_THREADS, 0, b->stream>>>(b->d_inst, b->phase, b->d_tile_inst,
                                                                               b->ctl);
     else
@@ -280,6 +364,17 @@ void launch_per_lattice_step(lbm_ace_batch* b)
     for (int i = 0; i < b->n; ++i) {
         const BatchInst& I = b->inst[i];
         const int rows = b->seq_rows[i];
+        if (b->quad) {
+            const dim3 grid((I.nx + Q32_COLS - 1) / Q32_COLS, (I.ny + rows - 1) / rows);
+            const size_t qs = sizeof(Quad32Smem);
+            if (b->model == LBM_ACE_MODEL_MODIFIED)
+                ace_batch_one_q<MODEL_MODIFIED><<<grid, Q32_THREADS, qs, b->stream>>>(b->d_inst, b->phase, i, rows,
+                                                                                    b->ctl, b->seq_part);
+            else
+                ace_batch_one_q<MODEL_CONSERVATIVE><<<grid, Q32_THREADS, qs, b->stream>>>(b->d_inst, b->phase, i,
+                                                                                        rows, b->ctl, b->seq_part);
+            continue;
+        }
         const dim3 grid(I.tiles_x, (I.ny + rows - 1) / rows);
         if (b->model == LBM_ACE_MODEL_MODIFIED)
             ace_batch_one<MODEL_MODIFIED><<<grid, PAIR_THREADS, 0, b->stream>>>(b->d_inst, b->phase, i, rows, b->ctl,
@@ -422,6 +517,11 @@ int lbm_ace_batch_init(const lbm_ace_params* params, int count, lbm_ace_batch** 
         b->own_stream = true;
     }
 
+    // work items: four-column strips of 128 columns when every nx allows them (the
+    // single-lattice library's FP32 kernel), else column-pair tiles of 256 columns
+    b->quad = true;
+    for (const auto& q : b->p) b->quad = b->quad && q.nx % 4 == 0;
+    b->cols = b->quad ? Q32_STRIP : PAIR_COLS;
     // memory: populations x2 and phi per lattice in one pool; tables; mass partials
     size_t elems = 0, tab = 0;
     long long max_tiles = 0;
@@ -429,7 +529,7 @@ int lbm_ace_batch_init(const lbm_ace_params* params, int count, lbm_ace_batch** 
         const size_t n = (size_t)q.nx * q.ny;
         elems += 19 * n + 3 * 64; // 2 x 9 planes + phi, each buffer padded to a 256-byte boundary
         tab += 2 * (size_t)(q.nx + q.ny) + 64;
-        max_tiles += (long long)((q.nx + PAIR_COLS - 1) / PAIR_COLS) * ((q.ny + kMinRows - 1) / kMinRows);
+        max_tiles += (long long)((q.nx + b->cols - 1) / b->cols) * ((q.ny + kMinRows - 1) / kMinRows);
     }
     b->max_tiles = (int)max_tiles;
     b->pool_elems = elems;
@@ -476,7 +576,7 @@ int lbm_ace_batch_init(const lbm_ace_params* params, int count, lbm_ace_batch** 
         I.T_period = q.T_period;
         I.end = LLONG_MAX;
         I.mass_part = mp;
-        mp += (size_t)((q.nx + PAIR_COLS - 1) / PAIR_COLS) * ((q.ny + kMinRows - 1) / kMinRows);
+        mp += (size_t)((q.nx + b->cols - 1) / b->cols) * ((q.ny + kMinRows - 1) / kMinRows);
         // Eq. 14 tables, as in the single-lattice library
         h.assign(2 * (q.nx + q.ny), 0.0f);
         for (int x = 0; x < q.nx; ++x) {
@@ -517,29 +617,46 @@ int lbm_ace_batch_init(const lbm_ace_params* params, int count, lbm_ace_batch** 
         BI(cudaStreamSynchronize(b->stream));
     }
     int occ = 0;
-    if (b->model == LBM_ACE_MODEL_MODIFIED)
+    const int qs = (int)sizeof(Quad32Smem);
+    if (b->quad) {
+        BI(cudaFuncSetAttribute(ace_batch_step_q<MODEL_MODIFIED>, cudaFuncAttributeMaxDynamicSharedMemorySize, qs));
+        BI(cudaFuncSetAttribute(ace_batch_step_q<MODEL_CONSERVATIVE>, cudaFuncAttributeMaxDynamicSharedMemorySize, qs));
+        BI(cudaFuncSetAttribute(ace_batch_one_q<MODEL_MODIFIED>, cudaFuncAttributeMaxDynamicSharedMemorySize, qs));
+        BI(cudaFuncSetAttribute(ace_batch_one_q<MODEL_CONSERVATIVE>, cudaFuncAttributeMaxDynamicSharedMemorySize, qs));
+        BI(cudaFuncSetAttribute(ace_step_quad<MODEL_MODIFIED, VelVortex<float>>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, qs));
+        BI(cudaFuncSetAttribute(ace_step_quad<MODEL_CONSERVATIVE, VelVortex<float>>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, qs));
+        BI(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ace_batch_step_q<MODEL_MODIFIED>, Q32_THREADS, qs));
+    } else if (b->model == LBM_ACE_MODEL_MODIFIED) {
         BI(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ace_batch_step<MODEL_MODIFIED>, PAIR_THREADS, 0));
-    else
+    } else {
         BI(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ace_batch_step<MODEL_CONSERVATIVE>, PAIR_THREADS, 0));
+    }
     b->grid = b->sms * std::max(1, occ);
     // the baseline launches each lattice as the single-lattice library would: rows per
-    // CTA for one wave of resident column-pair CTAs
+    // CTA for one wave of resident CTAs of the same kernel form (CTAs of four strips, or
+    // column-pair CTAs)
     {
         int pocc = 0;
-        if (b->model == LBM_ACE_MODEL_MODIFIED)
+        if (b->quad)
+            BI(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pocc, ace_batch_one_q<MODEL_MODIFIED>, Q32_THREADS, qs));
+        else if (b->model == LBM_ACE_MODEL_MODIFIED)
             BI(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&pocc, ace_step_pair<float, MODEL_MODIFIED, VelVortex<float>>,
                                                              PAIR_THREADS, 0));
         else
             BI(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
                 &pocc, ace_step_pair<float, MODEL_CONSERVATIVE, VelVortex<float>>, PAIR_THREADS, 0));
         const long long slots = (long long)b->sms * std::max(1, pocc);
+        const int cta_cols = b->quad ? Q32_COLS : PAIR_COLS;
         long long maxp = 1;
         b->seq_rows.resize(count);
         for (int i = 0; i < count; ++i) {
-            const int gx = (b->inst[i].nx + PAIR_COLS - 1) / PAIR_COLS;
+            const int gx = (b->inst[i].nx + cta_cols - 1) / cta_cols;
             const long long bands = std::max(1LL, slots / gx);
-            const int r = (int)std::max(4LL, std::min<long long>(b->inst[i].ny, (b->inst[i].ny + bands - 1) / bands));
-            b->seq_rows[i] = r;
+            long long r = std::max(4LL, std::min<long long>(b->inst[i].ny, (b->inst[i].ny + bands - 1) / bands));
+            if (b->quad) r = std::min(r, 4095LL);
+            b->seq_rows[i] = (int)r;
             maxp = std::max(maxp, (long long)gx * ((b->inst[i].ny + r - 1) / r));
         }
         BI(cudaMalloc(&b->seq_part, maxp * sizeof(double)));
@@ -590,6 +707,16 @@ int lbm_ace_batch_step_sequential(lbm_ace_batch* b, long long n)
             v.amp = I.amp;
             v.ct = float(std::cos(kPiB * (double)t / I.T_period));
             v.ctm1 = float(std::cos(kPiB * ((double)t - 1.0) / I.T_period));
+            if (b->quad) { // the single-lattice library's kernel for this lattice
+                const dim3 grid((I.nx + Q32_COLS - 1) / Q32_COLS, (I.ny + a.rows - 1) / a.rows);
+                if (b->model == LBM_ACE_MODEL_MODIFIED)
+                    ace_step_quad<MODEL_MODIFIED, VelVortex<float>><<<grid, Q32_THREADS, sizeof(Quad32Smem), b->stream>>>(
+                        a, v);
+                else
+                    ace_step_quad<MODEL_CONSERVATIVE, VelVortex<float>>
+                        <<<grid, Q32_THREADS, sizeof(Quad32Smem), b->stream>>>(a, v);
+                continue;
+            }
             dim3 grid(I.tiles_x, (I.ny + a.rows - 1) / a.rows);
             if (b->model == LBM_ACE_MODEL_MODIFIED)
                 ace_step_pair<float, MODEL_MODIFIED, VelVortex<float>><<<grid, PAIR_THREADS, 0, b->stream>>>(a, v);

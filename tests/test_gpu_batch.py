@@ -1,9 +1,12 @@
 """Batches of single-vortex lattices (persistent kernel, CUDA graph, autotuner).
 
 Every lattice of a batch must evolve exactly as the same lattice would alone: the
-batched kernel runs the same per-tile code (pair_tile); the only difference is where
-the phase cos(pi t / T) of Eq. 14 is computed (on the device in the graph, on the host
-for single lattices), which can move its last FP32 bit, hence the 1e-6 bound.
+batched kernel runs the single-lattice kernels' own tile code (quad32_strip on 128-column
+strips when every nx is a multiple of 4, pair_tile on 256-column tiles otherwise); the
+only difference is where the phase cos(pi t / T) of Eq. 14 is computed (on the device in
+the graph, on the host for single lattices), which can move its last FP32 bit, hence the
+1e-6 bound. The tests that take `specs` run both forms: SPECS holds a lattice with
+nx = 130, which keeps the batch on column-pair tiles; SPECS_Q has nx = 132 there.
 """
 import numpy as np
 import pytest
@@ -19,6 +22,20 @@ SPECS = [dict(nx=128, ny=128, tau=0.7, eps=0.8, U0=0.03, T_period=1500.0, xc=60.
          dict(nx=256, ny=256, tau=0.65, eps=1.0, U0=0.02, T_period=3000.0, xc=120.0, yc=140.0, R=40.0),
          dict(nx=384, ny=96, tau=0.8, eps=2.0, U0=0.04, T_period=3100.0, xc=200.0, yc=50.0, R=25.0),
          dict(nx=130, ny=41, tau=1.0, eps=0.6, U0=0.045, T_period=900.0, xc=60.0, yc=20.0, R=10.0)]
+SPECS_Q = SPECS[:4] + [dict(SPECS[4], nx=132)]
+FORMS = {"pair": SPECS, "quad": SPECS_Q}
+
+
+@pytest.fixture(params=["pair", "quad"])
+def form(request):
+    return request.param
+
+
+def expected_items(b, specs, form):
+    """Work items per step: 128-column strips (quad) or 256-column tiles (pair) of each
+    lattice's rows-tall bands."""
+    cols = 128 if form == "quad" else 256
+    return sum(-(-s["nx"] // cols) * -(-s["ny"] // b.info(i)["rows"]) for i, s in enumerate(specs))
 
 
 def standalone(spec, steps):
@@ -29,41 +46,44 @@ def standalone(spec, steps):
 
 
 @pytest.mark.parametrize("rows", [0, 8, 33])
-def test_batch_lattices_evolve_as_alone(rows):
-    specs = [dict(s, rows_per_cta=rows, vortex_sign=-1.0) for s in SPECS]
+def test_batch_lattices_evolve_as_alone(rows, form):
+    base = FORMS[form]
+    specs = [dict(s, rows_per_cta=rows, vortex_sign=-1.0) for s in base]
     with A.Batch(specs) as b:
+        assert b.info(0)["tiles"] == expected_items(b, base, form)  # the work-item form in use
         b.step(57)
         assert b.t == 57
-        for i, s in enumerate(SPECS):
+        for i, s in enumerate(base):
             ref, m0, m1 = standalone(s, 57)
             assert np.abs(b.phi(i) - ref).max() <= 1e-6
             assert b.mass(i) == pytest.approx(m1, rel=1e-6)
             assert abs(b.mass(i) - m0) <= 1e-5 * m0
 
 
-def test_graph_steps_match_sequential_launches():
-    specs = [dict(s, vortex_sign=-1.0) for s in SPECS]
+def test_graph_steps_match_sequential_launches(form):
+    specs = [dict(s, vortex_sign=-1.0) for s in FORMS[form]]
     with A.Batch(specs) as a, A.Batch(specs) as b:
         a.step(40)
         b.step_sequential(25)
         b.step(15)  # mixing the two modes keeps the device time in step
         assert a.t == b.t == 40
-        for i in range(len(SPECS)):
+        for i in range(len(specs)):
             assert np.abs(a.phi(i) - b.phi(i)).max() <= 1e-6
 
 
-def test_autotune_keeps_the_state_and_picks_candidate_heights():
-    specs = [dict(s, vortex_sign=-1.0) for s in SPECS]
+def test_autotune_keeps_the_state_and_picks_candidate_heights(form):
+    base = FORMS[form]
+    specs = [dict(s, vortex_sign=-1.0) for s in base]
     with A.Batch(specs) as b:
         b.step(10)
-        before = [b.phi(i) for i in range(len(SPECS))]
+        before = [b.phi(i) for i in range(len(base))]
         rows = b.autotune(steps_per_trial=2)
         assert b.t == 10
-        for i, s in enumerate(SPECS):
+        for i, s in enumerate(base):
             assert rows[i] in (8, 16, 32, 64, 128, 256) or rows[i] == s["ny"]
             assert np.array_equal(b.phi(i), before[i])
         b.step(20)
-        for i, s in enumerate(SPECS):
+        for i, s in enumerate(base):
             ref, _, _ = standalone(s, 30)
             assert np.abs(b.phi(i) - ref).max() <= 1e-6
 
@@ -108,37 +128,38 @@ def test_full_batch_of_256_lattices_at_sampled_lattices():
                 assert abs(b.mass(i) - m0) <= 1e-5 * m0
 
 
-def test_lattices_retire_at_their_own_end_step():
+def test_lattices_retire_at_their_own_end_step(form):
     """Uneven runs: each lattice advances until its own end step and then keeps its
     state, while the others go on; every lattice equals the same lattice run alone for
     exactly its own number of steps."""
     ends = [37, 60, 12, 60, 45]
-    specs = [dict(s, vortex_sign=-1.0) for s in SPECS]
+    base = FORMS[form]
+    specs = [dict(s, vortex_sign=-1.0) for s in base]
     with A.Batch(specs) as b:
         b.set_ends(ends)
         b.step(20)
         assert b.active()[0] == sum(e > 20 for e in ends)
         b.step(50)
         assert b.t == 70 and b.active() == (0, 0)
-        for i, s in enumerate(SPECS):
+        for i, s in enumerate(base):
             assert b.lattice_steps(i) == ends[i]
             ref, m0, m1 = standalone(s, ends[i])
             assert np.abs(b.phi(i) - ref).max() <= 1e-6
             assert b.mass(i) == pytest.approx(m1, rel=1e-6)
 
 
-def test_per_lattice_graph_and_host_launches_match_the_persistent_batch():
+def test_per_lattice_graph_and_host_launches_match_the_persistent_batch(form):
     """The two baselines -- one launch per lattice per step, captured in a graph or issued
     from the host -- give the batch's states, with retirement applied the same way."""
     ends = [30, 18, 41, 25, 9]
-    specs = [dict(s, vortex_sign=-1.0) for s in SPECS]
+    specs = [dict(s, vortex_sign=-1.0) for s in FORMS[form]]
     with A.Batch(specs) as a, A.Batch(specs) as b, A.Batch(specs) as c:
         for x in (a, b, c):
             x.set_ends(ends)
         a.step(45)
         b.step_per_lattice(45)
         c.step_sequential(45)
-        for i in range(len(SPECS)):
+        for i in range(len(specs)):
             assert b.lattice_steps(i) == c.lattice_steps(i) == ends[i]
             assert np.array_equal(a.phi(i), b.phi(i))
             assert np.abs(a.phi(i) - c.phi(i)).max() <= 1e-6
@@ -175,18 +196,19 @@ def test_set_ends_rejects_an_end_in_the_past():
         assert b.lattice_steps(0) == 10 and b.lattice_steps(1) == 15
 
 
-def test_autotune_sweeps_the_persistent_grid():
+def test_autotune_sweeps_the_persistent_grid(form):
     """The autotuner also picks the persistent grid: a whole number of CTAs per SM, at
     most the occupancy limit the batch starts with; the state is unaffected."""
     torch = pytest.importorskip("torch")
     sms = torch.cuda.get_device_properties(0).multi_processor_count
-    specs = [dict(s, vortex_sign=-1.0) for s in SPECS]
+    base = FORMS[form]
+    specs = [dict(s, vortex_sign=-1.0) for s in base]
     with A.Batch(specs) as b:
         g0 = b.info()["grid"]
         b.autotune(steps_per_trial=2)
         g = b.info()["grid"]
         assert g % sms == 0 and sms <= g <= g0
         b.step(12)
-        for i, s in enumerate(SPECS):
+        for i, s in enumerate(base):
             ref, _, _ = standalone(s, 12)
             assert np.abs(b.phi(i) - ref).max() <= 1e-6
