@@ -360,7 +360,9 @@ int lbm_ace_mass_noalloc(const void* values, int precision, long long count, dou
 const char* lbm_ace_last_error(const lbm_ace_ctx* c);
 const char* lbm_ace_status_string(int status);
 
-/* Free the context and its device memory. NULL is accepted. */
+/* Free the context: waits for its stream, then returns its device buffers to the
+ * device's pool in stream order on that stream (so the stream it was created with must
+ * still exist) and its result slot to the library. NULL is accepted. */
 void lbm_ace_destroy(lbm_ace_ctx* c);
 
 #ifdef __cplusplus
