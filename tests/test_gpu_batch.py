@@ -212,3 +212,19 @@ def test_autotune_sweeps_the_persistent_grid(form):
         for i, s in enumerate(base):
             ref, _, _ = standalone(s, 12)
             assert np.abs(b.phi(i) - ref).max() <= 1e-6
+
+
+def test_strip_batch_with_tiny_and_ragged_lattices():
+    """Four-column strips on lattices narrower than a strip (4, 8 columns), ragged last
+    strips (132, 260 = 2 x 128 + 4), and bands shorter than the default height, each
+    against the same lattice alone."""
+    sizes = [(4, 3), (8, 5), (132, 17), (260, 65), (16, 64)]
+    specs = [dict(nx=nx, ny=ny, tau=0.8, eps=1.0, U0=0.03, T_period=400.0, xc=0.5 * nx, yc=0.6 * ny,
+                  R=0.25 * min(nx, ny) + 1.0, vortex_sign=-1.0) for nx, ny in sizes]
+    with A.Batch(specs) as b:
+        assert b.info(0)["tiles"] == expected_items(b, specs, "quad")
+        b.step(23)
+        for i, s in enumerate(specs):
+            ref, m0, m1 = standalone({k: v for k, v in s.items() if k != "vortex_sign"}, 23)
+            assert np.abs(b.phi(i) - ref).max() <= 1e-6, (i, s["nx"], s["ny"])
+            assert b.mass(i) == pytest.approx(m1, rel=1e-6)
