@@ -175,14 +175,17 @@ int lbm_ace_release_cached_memory(int device);
  * 16-bit states: each value split into a multiple of 2^-16, summed exactly as an
  * integer, and a remainder below 2^-17 summed in FP32 (a thread that meets a value of
  * 2 or more in magnitude sums its values in FP64 instead), per-thread totals combined
- * with a compensated FP64 tree; relative error about 1e-14. One kernel launch; the
- * result reaches the host through mapped pinned memory. Synchronous. Returns
- * LBM_ACE_ENUMERIC (with *out set) when it is not finite. */
+ * with a compensated FP64 tree; relative error about 1e-14 (a thread adds a few hundred
+ * values at 2048^2; at the limit of 8192 values per thread, about 1e-10). One kernel
+ * launch; the result reaches the host through mapped pinned memory. Synchronous.
+ * Returns LBM_ACE_ENUMERIC (with *out set) when it is not finite. */
 int lbm_ace_mass(lbm_ace_ctx* c, double* out);
 
 /* Global mass sum_x phi(x, t-1) as reduced block by block inside the last
- * fused step (FP64 block partials, compensated final sum). Synchronous.
- * LBM_ACE_EINVAL before the first step. */
+ * fused step (FP64 block partials, compensated final sum; the quad kernels sum a
+ * thread's values in split parts whose FP32 remainder sum rounds by about 1e-14 of the
+ * total in the default launch shapes and up to about 1e-10 for bands thousands of rows
+ * tall). Synchronous. LBM_ACE_EINVAL before the first step. */
 int lbm_ace_step_mass(lbm_ace_ctx* c, double* out);
 
 /* Checkpoint: f[9*nx*ny] receives f_i(x, t) (after streaming, as in Eq. 9's

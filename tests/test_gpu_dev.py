@@ -181,3 +181,33 @@ def test_dev_default_kernel_choice(precision):
         assert g.launch_shape()[4] == A.KERNEL_DEV4
     with A.Lattice(nx=66, ny=16, precision=precision) as g:
         assert g.launch_shape()[4] == A.KERNEL_DEV
+
+
+@pytest.mark.parametrize("precision,variant,other", [(A.F32, A.KERNEL_QUAD, A.KERNEL_PAIR),
+                                                    (A.BF16DEV, A.KERNEL_DEV4, A.KERNEL_DEV)])
+def test_quad_kernels_take_at_most_4095_rows_per_band(precision, variant, other):
+    """The integer part of the quad kernels' step mass is exact for bands of at most 4095
+    rows: an explicit taller band is refused, the automatic shape never exceeds it, and a
+    4095-row band gives the column-pair kernels' states and step mass."""
+    nx, ny = 8, 4100
+    with pytest.raises(A.LbmAceError) as e:
+        A.Lattice(nx=nx, ny=ny, precision=precision, kernel_variant=variant, rows_per_cta=4096)
+    assert e.value.status == A.EINVAL
+    phi0 = W.random_smooth_phi(nx, ny, seed=5)
+    out = []
+    for v, rows in ((variant, 4095), (variant, 0), (other, 4095)):
+        with A.Lattice(nx=nx, ny=ny, precision=precision, kernel_variant=v, rows_per_cta=rows, phi0=phi0,
+                       T_period=900.0) as g:
+            shape = g.launch_shape()
+            assert shape[4] == v and shape[1] <= 4095
+            g.step(3)
+            f, pp = g.get_state()
+            out.append((f, pp, g.step_mass()))
+    # the step masses: a 4095-row band of this 8-wide lattice gives each of its two
+    # threads 4 x 4095 values, whose FP32 remainder sum (terms below 2^-17, a random walk
+    # of ~5e-4) rounds by ~1e-10 of the total; default launch shapes give a thread at
+    # most a few hundred values (~1e-14)
+    for f, pp, m in out[1:]:
+        assert np.array_equal(f, out[0][0]) and np.array_equal(pp, out[0][1])
+        assert m == pytest.approx(out[0][2], rel=1e-9)
+    assert out[0][2] == pytest.approx(float(out[0][1].astype(np.float32).astype(np.float64).sum()), rel=1e-9)
