@@ -43,6 +43,8 @@ KERNEL_NAME = {1: "ace_step", 2: "ace_step_bulk", 3: "ace_step_warp", 4: "ace_st
                6: "ace_step_tb2", 7: "ace_step_dev4", 8: "ace_step_quad"}
 STEPS_PER_LAUNCH = {6: 2}   # the two-step kernel: one launch advances two steps
 BYTES_PER_LUP = {"f64": 160, "f32": 80, "f16dev": 44, "bf16dev": 44}
+# arithmetic type of each storage form: the 16-bit deviation forms compute in FP32
+ARITH_DTYPE = {"f64": "f64", "f32": "f32", "f16dev": "f32", "bf16dev": "f32"}
 # FP64 step: 204 FP64 FLOP per node update (55.5 DFMA counted twice, 53.4 DADD, 40.0 DMUL;
 # ncu op counters of ace_step_pair<double>), bound by the FP64 pipe rather than by HBM.
 # Peak: GB300's nominal FP64 rate, 152 SMs x 2.07 GHz x 4 FLOP per clock = 1.259 TFLOP/s
@@ -363,7 +365,8 @@ def run_ours(args):
 
     line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": ARITH_DTYPE[args.precision], "storage": args.precision,
+            "data": "synthetic",
             "config": {**cfg, "launch": {"tile_x": shape[0], "rows_per_cta": shape[1],
                                          "grid": [shape[2], shape[3]],
                                          "kernel": {1: "ace_step (direct loads)",
