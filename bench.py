@@ -43,6 +43,7 @@ KERNEL_NAME = {1: "ace_step", 2: "ace_step_bulk", 3: "ace_step_warp", 4: "ace_st
                6: "ace_step_tb2", 7: "ace_step_dev4", 8: "ace_step_quad"}
 STEPS_PER_LAUNCH = {6: 2}   # the two-step kernel: one launch advances two steps
 BYTES_PER_LUP = {"f64": 160, "f32": 80, "f16dev": 44, "bf16dev": 44}
+HBM_NOMINAL_GBS = 7900.0  # GB300 HBM3e, nominal (context beside the measured copy peak)
 # arithmetic type of each storage form: the 16-bit deviation forms compute in FP32
 ARITH_DTYPE = {"f64": "f64", "f32": "f32", "f16dev": "f32", "bf16dev": "f32"}
 # FP64 step: 204 FP64 FLOP per node update (55.5 DFMA counted twice, 53.4 DADD, 40.0 DMUL;
@@ -349,6 +350,8 @@ def run_ours(args):
                 "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
                 else "fallback",
                 "algorithmic_bytes_per_launch": bpl, "lattice_updates_per_launch": spl * args.L * args.L,
+                "frac_of_nominal": achieved / HBM_NOMINAL_GBS, "nominal_gbs": HBM_NOMINAL_GBS,
+                "dram_gbs_moved": traffic / per_launch / 1e9 if traffic else None,
                 "kernel": "lbmace::" + KERNEL_NAME[shape[4]]}
     if args.precision == "f64":  # bound by the FP64 pipe: FLOP/s against the FP64 rate
         tf = F64_FLOP_PER_LUP * spl * args.L * args.L / per_launch / 1e12
