@@ -112,8 +112,13 @@ typedef struct lbm_ace_params {
     const double* v_field;
     lbm_ace_velocity_fn vel_fn;    /* LBM_ACE_VEL_CALLBACK */
     void* vel_user;
-    const double* phi0;  /* host [ny][nx] initial phi, copied at init; NULL selects the
-                            disk phi0 = 1/2 (1 + tanh((R - r) / (2 eps))) about (xc, yc) */
+    const double* phi0;  /* host [ny][nx] initial phi, read during init only; NULL selects
+                            the disk phi0 = 1/2 (1 + tanh((R - r) / (2 eps))) about (xc, yc).
+                            Every value must be finite and, for all precisions but
+                            LBM_ACE_F64 (whose phi is FP32), round to a finite FP32. Its
+                            upload runs while the host prepares the velocity, without
+                            waiting when phi0 is page-locked (cudaHostAlloc, cudaMallocHost,
+                            cudaHostRegister) */
     double xc, yc, R;
     int device;          /* CUDA device ordinal */
     void* stream;        /* cudaStream_t for all device work; NULL = the legacy default stream */
@@ -148,7 +153,10 @@ int lbm_ace_params_default(lbm_ace_params* p);
 
 /* Validate *p, allocate device state and initialise it (f_i = f_i^eq(phi0,
  * u(x, 0)), t = 0). Checks: nx, ny >= 3; tau > 0.5; eps > 0; M consistent; phi0
- * finite; the velocity source present. On success *out owns the context. */
+ * finite (in FP32 for the FP32-based precisions: fields of up to 65,536 values on the
+ * host before any device work, larger ones on the device right after the init kernel,
+ * with the smallest bad index in the message); the velocity source present. On success
+ * *out owns the context. */
 int lbm_ace_init(const lbm_ace_params* p, lbm_ace_ctx** out);
 
 /* Advance n >= 0 steps (Eq. 9, one fused kernel per step). Asynchronous on the
@@ -157,7 +165,10 @@ int lbm_ace_init(const lbm_ace_params* p, lbm_ace_ctx** out);
 int lbm_ace_step(lbm_ace_ctx* c, long long n);
 
 /* phi(x, t) = sum_i f_i(x, t) (Eq. 12) at the current time t, written to the
- * host array out[count], count == nx*ny. Synchronous. */
+ * host array out[count], count == nx*ny. Synchronous. A page-locked out (cudaHostAlloc,
+ * cudaMallocHost, cudaHostRegister; checked at its first and last byte) is written by
+ * the moment kernel itself through its mapped address; other memory through a device
+ * buffer and a copy. The values are the same either way. */
 int lbm_ace_get_phi(lbm_ace_ctx* c, double* out, size_t count);
 
 /* Device memory. A context's device buffers come from a stream-ordered memory pool

@@ -22,9 +22,11 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <mutex>
 #include <new>
 #include <string>
+#include <thread>
 #include <utility>
 #include <vector>
 
@@ -153,9 +155,11 @@ struct lbm_ace_ctx {
     double* red_part = nullptr; int n_red_part = 0;
     double* result = nullptr;
     PinnedSlot slot{nullptr, nullptr, 0}; // mapped pinned result block (acquire_slot)
-    double* hres = nullptr;     // its host address: the finishing kernels write results here
+    double* hres = nullptr;     // its host address: the finishing kernels write results to hres[0..1];
+                                // hres[4] takes the index the init's check of phi0 found
     double* hres_dev = nullptr; // its device address
-    double* scratch = nullptr; size_t scratch_elems = 0; // FP64 staging for state/phi copies
+    void* arena = nullptr;  // the one pool allocation every fixed buffer above and in vel is cut from
+    double* scratch = nullptr; size_t scratch_elems = 0; // FP64 staging for state/phi copies (own allocation)
     VelState vel;
     long long t = 0;
     bool stepped = false;
@@ -190,9 +194,11 @@ int fail(lbm_ace_ctx* c, int code, const char* fmt, ...)
                         "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__);  \
     } while (0)
 
-// A device buffer of the context from the device's pool (device_pool), ready for use on
-// any stream when this returns (the allocation is ordered on the context's stream, which
-// is then synchronised: reused blocks may come from another context's stream).
+// A device buffer of the context from the device's pool (device_pool), ordered on the
+// context's stream. Every use of a context's buffers (kernels, copies, memsets) is issued
+// on that stream, so none needs a synchronisation here; a block that another context freed
+// on another stream is reused after that free, by the dependencies the pool's default
+// reuse policies give the allocation.
 template <typename P>
 int pool_alloc(lbm_ace_ctx* c, P** ptr, size_t bytes)
 {
@@ -201,7 +207,6 @@ int pool_alloc(lbm_ace_ctx* c, P** ptr, size_t bytes)
     void* q = nullptr;
     CK(c, cudaMallocFromPoolAsync(&q, bytes, pool, c->stream));
     *ptr = static_cast<P*>(q);
-    CK(c, cudaStreamSynchronize(c->stream));
     return LBM_ACE_OK;
 }
 #define PA(ctx, ptr, bytes)                              \
@@ -484,31 +489,61 @@ void launch_init_t(lbm_ace_ctx* c, const double* dphi0, double t0)
     }
 }
 
+// The four single-vortex tables (sx2, s2x over x; sy2, s2y over y) sit back to back in one
+// block of the context's allocation, each padded to 256 bytes.
+size_t pad256(size_t b) { return (b + 255) & ~size_t(255); }
+size_t vortex_table_bytes(int nx, int ny, size_t elem) { return 2 * pad256(nx * elem) + 2 * pad256(ny * elem); }
+
+// Fill the tables at c->vel.sx2 (a block of vortex_table_bytes) with one copy from the host.
 template <typename T>
 int fill_vortex_tables(lbm_ace_ctx* c)
 {
     const int nx = c->p.nx, ny = c->p.ny;
-    std::vector<T> sx2(nx), s2x(nx), sy2(ny), s2y(ny);
+    const size_t ox = pad256(nx * sizeof(T)) / sizeof(T), oy = pad256(ny * sizeof(T)) / sizeof(T);
+    std::vector<T> h(vortex_table_bytes(nx, ny, sizeof(T)) / sizeof(T), T(0));
+    T* sx2 = h.data(); T* s2x = sx2 + ox; T* sy2 = s2x + ox; T* s2y = sy2 + oy;
     for (int x = 0; x < nx; ++x) {
         const double s = std::sin(kPi * x / nx);
         sx2[x] = T(s * s);
         s2x[x] = T(std::sin(2.0 * kPi * x / nx));
     }
-    for (int y = 0; y < ny; ++y) {
-        const double s = std::sin(kPi * y / ny);
-        sy2[y] = T(s * s);
-        s2y[y] = T(std::sin(2.0 * kPi * y / ny));
+    if (ny == nx) { // the same expressions of the same arguments
+        std::copy(sx2, sx2 + nx, sy2);
+        std::copy(s2x, s2x + nx, s2y);
+    } else {
+        for (int y = 0; y < ny; ++y) {
+            const double s = std::sin(kPi * y / ny);
+            sy2[y] = T(s * s);
+            s2y[y] = T(std::sin(2.0 * kPi * y / ny));
+        }
     }
-    PA(c, &c->vel.sx2, nx * sizeof(T));
-    PA(c, &c->vel.s2x, nx * sizeof(T));
-    PA(c, &c->vel.sy2, ny * sizeof(T));
-    PA(c, &c->vel.s2y, ny * sizeof(T));
-    CK(c, cudaMemcpy(c->vel.sx2, sx2.data(), nx * sizeof(T), cudaMemcpyHostToDevice));
-    CK(c, cudaMemcpy(c->vel.s2x, s2x.data(), nx * sizeof(T), cudaMemcpyHostToDevice));
-    CK(c, cudaMemcpy(c->vel.sy2, sy2.data(), ny * sizeof(T), cudaMemcpyHostToDevice));
-    CK(c, cudaMemcpy(c->vel.s2y, s2y.data(), ny * sizeof(T), cudaMemcpyHostToDevice));
+    T* d = static_cast<T*>(c->vel.sx2);
+    c->vel.s2x = d + ox;
+    c->vel.sy2 = d + 2 * ox;
+    c->vel.s2y = d + 2 * ox + oy;
+    // pageable source: the copy has staged its bytes when it returns
+    CK(c, cudaMemcpyAsync(d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, c->stream));
     return LBM_ACE_OK;
 }
+
+// Offsets of a context's fixed buffers inside its one pool allocation, each 256-byte
+// aligned: one cudaMallocFromPoolAsync costs about 7 us of host time on GB300, and
+// creating a lattice took ten of them.
+struct Carve {
+    std::vector<std::function<void(char*)>> set;
+    size_t total = 0;
+    template <typename P>
+    void add(P** ptr, size_t bytes)
+    {
+        const size_t off = total;
+        set.push_back([ptr, off](char* base) { *ptr = reinterpret_cast<P*>(base + off); });
+        total += pad256(bytes);
+    }
+    void assign(void* base) const
+    {
+        for (const auto& f : set) f(static_cast<char*>(base));
+    }
+};
 
 // Occupancy (resident CTAs per SM) of the chosen step kernel; opts the bulk kernel
 // into its dynamic shared memory.
@@ -643,6 +678,26 @@ int callback_upload(lbm_ace_ctx* c, double t, int pair)
 
 int check_device_error(lbm_ace_ctx* c);
 
+// The device address of the host range [p, p + bytes) when the range is page-locked host
+// memory (cudaHostAlloc, cudaMallocHost or cudaHostRegister; with unified addressing such
+// memory is mapped for every device), checked at its first and last byte; nullptr for
+// pageable or device memory, which the callers copy through cudaMemcpyAsync instead.
+const void* mapped_host(const void* p, size_t bytes)
+{
+    if (!p || bytes == 0) return nullptr;
+    const char* q = static_cast<const char*>(p);
+    cudaPointerAttributes a{}, b{};
+    if (cudaPointerGetAttributes(&a, q) != cudaSuccess || cudaPointerGetAttributes(&b, q + bytes - 1) != cudaSuccess) {
+        (void)cudaGetLastError(); // clear the query's own error
+        return nullptr;
+    }
+    if (a.type != cudaMemoryTypeHost || b.type != cudaMemoryTypeHost || !a.devicePointer || !b.devicePointer)
+        return nullptr;
+    if (static_cast<const char*>(b.devicePointer) - static_cast<const char*>(a.devicePointer) != (ptrdiff_t)(bytes - 1))
+        return nullptr;
+    return a.devicePointer;
+}
+
 // The sum and the wait-failure flag, which the finishing kernel wrote to the mapped host
 // block (write_result): no copy, only the stream synchronisation.
 int fetch_result(lbm_ace_ctx* c, double* out)
@@ -698,22 +753,21 @@ struct DeviceGuard {
     ~DeviceGuard() { if (prev >= 0) cudaSetDevice(prev); }
 };
 
-// phi(x, t) of the current state into c->scratch (FP64), on the context's stream.
-int phi_to_scratch(lbm_ace_ctx* c)
+// phi(x, t) of the current state as FP64 into dst (device memory, or the mapped address
+// of page-locked host memory), on the context's stream.
+int phi_to(lbm_ace_ctx* c, double* dst)
 {
     const size_t n = (size_t)c->p.nx * c->p.ny;
-    int rc = ensure_scratch(c, n);
-    if (rc) return rc;
     const int gr = grid_for((long long)n, c->sms);
     const unsigned short* gs = (const unsigned short*)c->f[c->cur];
     switch (c->p.precision) {
-    case LBM_ACE_F64: ace_moment<double><<<gr, 256, 0, c->stream>>>((const double*)c->f[c->cur], c->scratch, c->p.nx, c->p.ny); break;
-    case LBM_ACE_F32: ace_moment<float><<<gr, 256, 0, c->stream>>>((const float*)c->f[c->cur], c->scratch, c->p.nx, c->p.ny); break;
+    case LBM_ACE_F64: ace_moment<double><<<gr, 256, 0, c->stream>>>((const double*)c->f[c->cur], dst, c->p.nx, c->p.ny); break;
+    case LBM_ACE_F32: ace_moment<float><<<gr, 256, 0, c->stream>>>((const float*)c->f[c->cur], dst, c->p.nx, c->p.ny); break;
     case LBM_ACE_F16DEV:
-        ace_pull_state_dev<__half><<<gr, 256, 0, c->stream>>>(gs, c->phi2[c->pcur], nullptr, c->scratch, nullptr, c->p.nx, c->p.ny);
+        ace_pull_state_dev<__half><<<gr, 256, 0, c->stream>>>(gs, c->phi2[c->pcur], nullptr, dst, nullptr, c->p.nx, c->p.ny);
         break;
     default:
-        ace_pull_state_dev<__nv_bfloat16><<<gr, 256, 0, c->stream>>>(gs, c->phi2[c->pcur], nullptr, c->scratch, nullptr,
+        ace_pull_state_dev<__nv_bfloat16><<<gr, 256, 0, c->stream>>>(gs, c->phi2[c->pcur], nullptr, dst, nullptr,
                                                                      c->p.nx, c->p.ny);
         break;
     }
@@ -721,8 +775,16 @@ int phi_to_scratch(lbm_ace_ctx* c)
     return LBM_ACE_OK;
 }
 
+// phi(x, t) into c->scratch (FP64).
+int phi_to_scratch(lbm_ace_ctx* c)
+{
+    const int rc = ensure_scratch(c, (size_t)c->p.nx * c->p.ny);
+    return rc ? rc : phi_to(c, c->scratch);
+}
+
 // Smallest index k with v[k] not finite, into *first (which starts at ULLONG_MAX).
-__global__ void ace_first_nonfinite(const double* __restrict__ v, long long n, unsigned long long* first)
+template <typename T>
+__global__ void ace_first_nonfinite(const T* __restrict__ v, long long n, unsigned long long* first)
 {
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
         if (!isfinite(v[k])) atomicMin(first, (unsigned long long)k);
@@ -806,11 +868,8 @@ void lbm_ace_destroy(lbm_ace_ctx* c)
     if (!c) return;
     DeviceGuard g(c->dev);
     if (c->stream) cudaStreamSynchronize(c->stream); else cudaDeviceSynchronize();
-    void* bufs[] = {c->f[0], c->f[1], c->phi, c->phi_alt, c->phi2[0], c->phi2[1], c->step_part, c->red_part, c->result,
-                    c->scratch,
-                    c->vel.sx2, c->vel.s2x, c->vel.sy2, c->vel.s2y,
-                    c->vel.pu[0], c->vel.pu[1], c->vel.pv[0], c->vel.pv[1]};
-    for (void* b : bufs) if (b) cudaFreeAsync(b, c->stream); // back to the device's pool
+    for (void* b : {c->arena, static_cast<void*>(c->scratch)})
+        if (b) cudaFreeAsync(b, c->stream); // back to the device's pool
     if (c->slot.host) release_slot(c->slot);
     delete c;
 }
@@ -826,25 +885,6 @@ static int init_impl(lbm_ace_ctx* c, const lbm_ace_params* p)
     const int nx = p->nx, ny = p->ny;
     const size_t n = (size_t)nx * ny;
     c->elem = is_f64(c) ? sizeof(double) : (is_dev(c) ? 2 : sizeof(float));
-
-    PA(c, &c->f[0], 9 * n * c->elem);
-    PA(c, &c->f[1], 9 * n * c->elem);
-    if (is_dev(c)) {
-        PA(c, &c->phi2[0], n * sizeof(float));
-        PA(c, &c->phi2[1], n * sizeof(float));
-    } else {
-        PA(c, &c->phi, n * c->elem);
-    }
-    if (p->kernel_variant == 6) PA(c, &c->phi_alt, n * sizeof(float));
-    // result block: the reduced sum, a spare double, the device wait-failure flag, and the
-    // ticket counter of the mass reductions that finish in their last CTA
-    PA(c, &c->result, 4 * sizeof(double));
-    c->dev_err = reinterpret_cast<int*>(c->result + 2);
-
-    CK(c, cudaMemsetAsync(c->result, 0, 4 * sizeof(double), c->stream));
-    CK(c, acquire_slot(&c->slot));
-    c->hres = c->slot.host;
-    c->hres_dev = c->slot.dev;
 
     // kernel variant, automatic choice measured on GB300 (FP32): four columns per thread in warp strips
     // up to 2^23 nodes (1024^2: 71k against 67k MLUPS for column pairs; 2048^2: 80k against
@@ -894,7 +934,6 @@ static int init_impl(lbm_ace_ctx* c, const lbm_ace_params* p)
     c->rows = rows;
     c->grid_y = (ny + rows - 1) / rows;
     c->n_step_part = c->grid_x * c->grid_y;
-    PA(c, &c->step_part, c->n_step_part * sizeof(double));
     // global mass: FP64 states by the compensated grid-stride kernel, the others by the
     // fused kernels sized to one wave of resident CTAs (FP32: 4 CTAs/SM of the 6 that
     // fit, measured 35.0 against 36.9 us at 2048^2; 16-bit: all that fit)
@@ -911,21 +950,55 @@ static int init_impl(lbm_ace_ctx* c, const lbm_ace_params* p)
         c->n_red_part = p->precision == LBM_ACE_F64 ? grid_for(9 * (long long)n, c->sms)
                                                     : mass_reduction_grid(c->sms, rocc, 10 * (long long)n);
     }
-    PA(c, &c->red_part, c->n_red_part * sizeof(double));
+
+    // every fixed buffer of the context in one allocation from the device's pool
+    const int pairs = p->velocity_kind == LBM_ACE_VEL_CALLBACK ? 2 : p->velocity_kind == LBM_ACE_VEL_FIELD ? 1 : 0;
+    {
+        Carve cv;
+        cv.add(&c->f[0], 9 * n * c->elem);
+        cv.add(&c->f[1], 9 * n * c->elem);
+        if (is_dev(c)) {
+            cv.add(&c->phi2[0], n * sizeof(float));
+            cv.add(&c->phi2[1], n * sizeof(float));
+        } else {
+            cv.add(&c->phi, n * c->elem);
+        }
+        if (c->variant == 6) cv.add(&c->phi_alt, n * sizeof(float));
+        // result block: the reduced sum, a spare double, the device wait-failure flag, and
+        // the ticket counter of the mass reductions that finish in their last CTA
+        cv.add(&c->result, 4 * sizeof(double));
+        cv.add(&c->step_part, c->n_step_part * sizeof(double));
+        cv.add(&c->red_part, c->n_red_part * sizeof(double));
+        if (p->velocity_kind == LBM_ACE_VEL_SINGLE_VORTEX) // FP32 tables for 16-bit storage
+            cv.add(&c->vel.sx2, vortex_table_bytes(nx, ny, is_f64(c) ? sizeof(double) : sizeof(float)));
+        for (int k = 0; k < pairs; ++k) {
+            cv.add(&c->vel.pu[k], n * sizeof(double));
+            cv.add(&c->vel.pv[k], n * sizeof(double));
+        }
+        PA(c, &c->arena, cv.total);
+        cv.assign(c->arena);
+    }
+    c->dev_err = reinterpret_cast<int*>(c->result + 2);
+    CK(c, cudaMemsetAsync(c->result, 0, 4 * sizeof(double), c->stream));
+    CK(c, acquire_slot(&c->slot));
+    c->hres = c->slot.host;
+    c->hres_dev = c->slot.dev;
+
+    // initial phi first: its upload (asynchronous from page-locked memory) runs while the
+    // host computes the velocity tables below
+    rc = ensure_scratch(c, n);
+    if (rc) return rc;
+    if (p->phi0) CK(c, cudaMemcpyAsync(c->scratch, p->phi0, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
 
     // velocity
     if (p->velocity_kind == LBM_ACE_VEL_SINGLE_VORTEX) {
-        rc = is_f64(c) ? fill_vortex_tables<double>(c) : fill_vortex_tables<float>(c); // FP32 for 16-bit storage
+        rc = is_f64(c) ? fill_vortex_tables<double>(c) : fill_vortex_tables<float>(c);
         if (rc) return rc;
-    } else if (p->velocity_kind == LBM_ACE_VEL_FIELD || p->velocity_kind == LBM_ACE_VEL_CALLBACK) {
-        const int pairs = p->velocity_kind == LBM_ACE_VEL_CALLBACK ? 2 : 1;
-        for (int k = 0; k < pairs; ++k) {
-            PA(c, &c->vel.pu[k], n * sizeof(double));
-            PA(c, &c->vel.pv[k], n * sizeof(double));
-        }
+    } else if (pairs > 0) {
         if (pairs == 1) {
-            CK(c, cudaMemcpy(c->vel.pu[0], p->u_field, n * sizeof(double), cudaMemcpyHostToDevice));
-            CK(c, cudaMemcpy(c->vel.pv[0], p->v_field, n * sizeof(double), cudaMemcpyHostToDevice));
+            // the caller's arrays are read by the time init returns (it ends synchronised)
+            CK(c, cudaMemcpyAsync(c->vel.pu[0], p->u_field, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+            CK(c, cudaMemcpyAsync(c->vel.pv[0], p->v_field, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
         } else {
             c->vel.hu.assign(n, 0.0);
             c->vel.hv.assign(n, 0.0);
@@ -935,24 +1008,35 @@ static int init_impl(lbm_ace_ctx* c, const lbm_ace_params* p)
         }
     }
 
-    // initial phi: host array or the disk
-    rc = ensure_scratch(c, n);
-    if (rc) return rc;
-    unsigned long long* first_bad = reinterpret_cast<unsigned long long*>(c->result + 1);
-    const bool check_on_device = p->phi0 && n > kHostCheckMax;
-    if (p->phi0) {
-        CK(c, cudaMemcpyAsync(c->scratch, p->phi0, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-        if (check_on_device) { // large phi0: checked where it already is, instead of a host pass over it
-            CK(c, cudaMemsetAsync(first_bad, 0xff, sizeof(unsigned long long), c->stream));
-            ace_first_nonfinite<<<grid_for((long long)n, c->sms), 256, 0, c->stream>>>(c->scratch, (long long)n, first_bad);
-        }
-    } else {
+    // without phi0: the disk, built on the host
+    const double* src = c->scratch;
+    if (!p->phi0) {
         std::vector<double> h(n);
-        for (int y = 0; y < ny; ++y)
-            for (int x = 0; x < nx; ++x) {
-                const double r = std::sqrt((x - p->xc) * (x - p->xc) + (y - p->yc) * (y - p->yc));
-                h[(size_t)y * nx + x] = 0.5 * (1.0 + std::tanh((p->R - r) / (2.0 * p->eps)));
+        auto disk_rows = [&](int ya, int yb) {
+            for (int y = ya; y < yb; ++y)
+                for (int x = 0; x < nx; ++x) {
+                    const double r = std::sqrt((x - p->xc) * (x - p->xc) + (y - p->yc) * (y - p->yc));
+                    h[(size_t)y * nx + x] = 0.5 * (1.0 + std::tanh((p->R - r) / (2.0 * p->eps)));
+                }
+        };
+        // row bands on host threads for large lattices (one Grace core takes 26 ms for
+        // 2048^2); every value is the same expression whichever thread computes it
+        const unsigned hw = std::thread::hardware_concurrency();
+        const int nt = n >= (size_t(1) << 18) ? (int)std::min(16u, std::max(1u, hw)) : 1;
+        std::vector<std::thread> pool;
+        const int own = (int)((long long)ny / nt); // rows [0, own) are this thread's
+        int start = own;                           // the first row no thread has taken
+        try {
+            for (int k = 1; k < nt; ++k) {
+                const int yb = (int)((long long)ny * (k + 1) / nt);
+                pool.emplace_back(disk_rows, start, yb);
+                start = yb;
             }
+        } catch (...) { // no further thread to be had: the rest on this one
+        }
+        disk_rows(0, own);
+        disk_rows(start, ny); // empty when every band got its thread
+        for (auto& t : pool) t.join();
         CK(c, cudaMemcpyAsync(c->scratch, h.data(), n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
         CK(c, cudaStreamSynchronize(c->stream));
     }
@@ -960,19 +1044,35 @@ static int init_impl(lbm_ace_ctx* c, const lbm_ace_params* p)
     c->t = 0;
     c->pcur = 0;
     switch (p->precision) {
-    case LBM_ACE_F64: launch_init_t<double>(c, c->scratch, 0.0); break;
-    case LBM_ACE_F32: launch_init_t<float>(c, c->scratch, 0.0); break;
-    case LBM_ACE_F16DEV: launch_init_dev<__half>(c, c->scratch, 0.0); break;
-    default: launch_init_dev<__nv_bfloat16>(c, c->scratch, 0.0); break;
+    case LBM_ACE_F64: launch_init_t<double>(c, src, 0.0); break;
+    case LBM_ACE_F32: launch_init_t<float>(c, src, 0.0); break;
+    case LBM_ACE_F16DEV: launch_init_dev<__half>(c, src, 0.0); break;
+    default: launch_init_dev<__nv_bfloat16>(c, src, 0.0); break;
     }
     c->fresh = true;
     CK(c, cudaGetLastError());
-    if (check_on_device) {
-        unsigned long long bad = 0;
-        CK(c, cudaMemcpyAsync(&bad, first_bad, sizeof bad, cudaMemcpyDeviceToHost, c->stream));
-        CK(c, cudaStreamSynchronize(c->stream));
-        if (bad != ~0ULL) return fail(c, LBM_ACE_EINVAL, "phi0[%llu] is not finite", bad);
+    // a large phi0 is checked where it now is, in the phi plane the init wrote in the
+    // storage precision (smaller ones were checked on the host before any device work)
+    if (p->phi0 && n > kHostCheckMax) {
+        unsigned long long* first_bad = reinterpret_cast<unsigned long long*>(c->result + 1);
+        CK(c, cudaMemsetAsync(first_bad, 0xff, sizeof(unsigned long long), c->stream));
+        const int gr = grid_for((long long)n, c->sms);
+        if (is_f64(c))
+            ace_first_nonfinite<double><<<gr, 256, 0, c->stream>>>((const double*)c->phi, (long long)n, first_bad);
+        else
+            ace_first_nonfinite<float><<<gr, 256, 0, c->stream>>>(is_dev(c) ? c->phi2[c->pcur] : (const float*)c->phi,
+                                                                (long long)n, first_bad);
+        CK(c, cudaGetLastError());
+        // read back into the context's page-locked result slot (an asynchronous copy; a
+        // pageable destination would add a synchronisation of its own)
+        unsigned long long* hbad = reinterpret_cast<unsigned long long*>(c->hres + 4);
+        CK(c, cudaMemcpyAsync(hbad, first_bad, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
         CK(c, cudaMemsetAsync(first_bad, 0, sizeof(unsigned long long), c->stream));
+        CK(c, cudaStreamSynchronize(c->stream));
+        const unsigned long long bad = *hbad;
+        if (bad != ~0ULL)
+            return fail(c, LBM_ACE_EINVAL, is_f64(c) ? "phi0[%llu] is not finite" : "phi0[%llu] is not finite as FP32", bad);
+        return LBM_ACE_OK;
     }
     CK(c, cudaStreamSynchronize(c->stream));
     return LBM_ACE_OK;
@@ -1025,9 +1125,15 @@ int lbm_ace_init(const lbm_ace_params* p, lbm_ace_ctx** out)
     }
     if (p->phi0 && (size_t)p->nx * p->ny <= kHostCheckMax) { // larger fields are checked on the device
         const size_t n = (size_t)p->nx * p->ny;
-        for (size_t k = 0; k < n; ++k)
+        // the FP32-based forms keep phi in FP32: a value must also round to a finite FP32
+        // (magnitude below 2^128 - 2^103; round to nearest takes the midpoint up to infinity)
+        const bool f64 = p->precision == LBM_ACE_F64;
+        for (size_t k = 0; k < n; ++k) {
             if (!std::isfinite(p->phi0[k]))
                 return fail(nullptr, LBM_ACE_EINVAL, "phi0[%zu] is not finite", k);
+            if (!f64 && !(std::fabs(p->phi0[k]) < 0x1p128 - 0x1p103))
+                return fail(nullptr, LBM_ACE_EINVAL, "phi0[%zu] is not finite as FP32", k);
+        }
     } else if (!p->phi0 && (!std::isfinite(p->xc) || !std::isfinite(p->yc) || !std::isfinite(p->R))) {
         return fail(nullptr, LBM_ACE_EINVAL, "disk centre/radius not finite");
     }
@@ -1108,9 +1214,12 @@ int lbm_ace_get_phi(lbm_ace_ctx* c, double* out, size_t count)
     const size_t n = (size_t)c->p.nx * c->p.ny;
     if (!out || count != n) return fail(c, LBM_ACE_EINVAL, "out must hold nx*ny = %zu values (got %zu)", n, count);
     DeviceGuard g(c->dev);
-    const int rc = phi_to_scratch(c);
+    // page-locked out: the moment kernel writes it through its mapped address (one pass
+    // over the host link, no device staging); else staged in c->scratch and copied
+    double* mapped = static_cast<double*>(const_cast<void*>(mapped_host(out, n * sizeof(double))));
+    const int rc = mapped ? phi_to(c, mapped) : phi_to_scratch(c);
     if (rc) return rc;
-    CK(c, cudaMemcpyAsync(out, c->scratch, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if (!mapped) CK(c, cudaMemcpyAsync(out, c->scratch, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
     return check_device_error(c);
 }

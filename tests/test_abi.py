@@ -97,6 +97,24 @@ def test_non_finite_phi0_is_rejected():
     assert e.value.status == A.EINVAL and "phi0[28]" in str(e.value)
 
 
+@pytest.mark.parametrize("precision", [1, 2, 3])
+def test_phi0_beyond_fp32_range_is_rejected_for_fp32_storage(precision):
+    """The FP32-based forms keep phi in FP32: a value that rounds to infinity there
+    (|v| >= 2^128 - 2^103) is rejected before any device work; one just below is not."""
+    phi0 = np.full((8, 8), 0.5)
+    phi0[2, 5] = -(2.0 ** 128 - 2.0 ** 103)
+    with pytest.raises(A.LbmAceError) as e:
+        A.Lattice(nx=8, ny=8, phi0=phi0, precision=precision)
+    assert e.value.status == A.EINVAL and "phi0[21] is not finite as FP32" in str(e.value)
+    phi0[2, 5] = -np.nextafter(2.0 ** 128 - 2.0 ** 103, 0.0)  # rounds to -FLT_MAX
+    assert np.isfinite(np.float32(phi0[2, 5]))
+    for p in (precision, 0):  # and FP64 storage takes any finite value
+        try:
+            A.Lattice(nx=8, ny=8, phi0=phi0 if p else np.where(phi0 == 0.5, 0.5, -1e300), precision=p)
+        except A.LbmAceError as e:
+            assert e.status in (A.ECUDA, A.ENOMEM), e
+
+
 def test_consistent_mobility_is_accepted_by_validation():
     """M = c_s^2 (tau - 1/2) passes validation (it then fails only for want of a GPU here)."""
     try:
