@@ -76,6 +76,8 @@ struct StepArgs {
     int rows;                  // rows per CTA
     int first;                 // t == 0: no time-derivative term
     int tdir;                  // t & 1: march direction of the row bands (column-pair kernels)
+    int l2_keep = 0;           // FP32 quad kernel: 1 = f* stored with an L2 evict_last policy on a
+                               // quarter of the lines (populations of about the L2's size)
     T omega;                   // 1 / tau
     T fpref;                   // 1 - 1 / (2 tau)
     T eps, inv_eps, inv4eps;   // eps, 1/eps, 1/(4 eps)

@@ -167,6 +167,7 @@ struct lbm_ace_ctx {
     int rows = 0, grid_x = 0, grid_y = 0;
     int variant = 1;        // 1: ace_step (direct loads), 2: ace_step_bulk
     int dev4_ctas = 3;      // resident CTAs per SM the 16-bit quad kernel is compiled for
+    int l2_keep = 0;        // variant 8: f* stores keep part of their lines in L2 (StepArgs::l2_keep)
     int tile_x = TILE_X;
     size_t smem = 0;        // dynamic shared memory of the chosen step kernel
     int* dev_err = nullptr; // set by a kernel whose bounded wait gave up (inside the result block)
@@ -238,6 +239,7 @@ StepArgs<T> make_args(lbm_ace_ctx* c)
     a.rows = c->rows;
     a.first = c->fresh;
     a.tdir = (int)(c->t & 1);
+    a.l2_keep = c->l2_keep;
     a.omega = T(1.0 / c->p.tau);
     a.fpref = T(1.0 - 0.5 / c->p.tau);
     a.eps = T(c->p.eps);
@@ -898,6 +900,15 @@ static int init_impl(lbm_ace_ctx* c, const lbm_ace_params* p)
         c->variant = nx % 2 == 0 ? 4 : 1;
     // the deviation-storage kernels: four columns per thread when nx allows, else pairs
     if (is_dev(c)) c->variant = p->kernel_variant != 0 ? p->kernel_variant : (nx % 4 == 0 ? 7 : 5);
+    // the FP32 quad kernel keeps part of the f* it stores in L2 when one population
+    // buffer is between half and twice the L2's size (faster from 1536^2 to 2560^2 on
+    // GB300, slower far above; ace_step_quad.cuh)
+    if (c->variant == 8) {
+        int l2 = 0;
+        CK(c, cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, c->dev));
+        const double fbytes = 9.0 * (double)n * (double)c->elem;
+        c->l2_keep = l2 > 0 && fbytes > 0.5 * l2 && fbytes <= 2.0 * l2;
+    }
 
     // launch shape of the fused step: one wave of resident CTAs when possible
     int occ = 0;
