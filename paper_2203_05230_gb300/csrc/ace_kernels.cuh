@@ -39,6 +39,40 @@ namespace lbmace {
 
 constexpr int TILE_X = 128;
 
+// L2 eviction priority of a kernel's stores, set by the host per lattice (StepArgs::
+// l2_keep): a policy from createpolicy rides on each st.global.L2::cache_hint. A step
+// reads first the rows the step before wrote last (alternating march), and what it reads
+// is dead once read, so letting written lines outlast read ones turns more of the next
+// step's reads into L2 hits where the data is of about the L2's size (measured on GB300).
+constexpr int L2_KEEP_F = 1, L2_KEEP_PHI = 2;
+
+// evict_last on `frac` of the lines when keep, else the normal priority (both policies
+// are made and one is selected: no branch)
+__device__ __forceinline__ unsigned long long l2_store_policy_quarter(bool keep)
+{
+    unsigned long long last, normal;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 0.25;" : "=l"(last));
+    asm("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(normal));
+    return keep ? last : normal;
+}
+__device__ __forceinline__ unsigned long long l2_store_policy_all(bool keep)
+{
+    unsigned long long last, normal;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(last));
+    asm("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(normal));
+    return keep ? last : normal;
+}
+__device__ __forceinline__ void st_policy(float* p, float4 v, unsigned long long policy)
+{
+    asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;"
+                 :: "l"(p), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "l"(policy) : "memory");
+}
+__device__ __forceinline__ void st_policy(float* p, float2 v, unsigned long long policy)
+{
+    asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;"
+                 :: "l"(p), "f"(v.x), "f"(v.y), "l"(policy) : "memory");
+}
+
 // D2Q9 velocity set and weights (Section 2.2, after Eq. 10):
 // 0:(0,0) 1:(1,0) 2:(0,1) 3:(-1,0) 4:(0,-1) 5:(1,1) 6:(-1,1) 7:(-1,-1) 8:(1,-1)
 __host__ __device__ constexpr int cx_of(int i)
@@ -76,8 +110,9 @@ struct StepArgs {
     int rows;                  // rows per CTA
     int first;                 // t == 0: no time-derivative term
     int tdir;                  // t & 1: march direction of the row bands (column-pair kernels)
-    int l2_keep = 0;           // FP32 quad kernel: 1 = f* stored with an L2 evict_last policy on a
-                               // quarter of the lines (populations of about the L2's size)
+    int l2_keep = 0;           // L2 priority of the stores (bits; 0 = normal): L2_KEEP_F = f* of
+                               // the FP32 quad kernel evict_last on a quarter of the lines,
+                               // L2_KEEP_PHI = the phi plane evict_last (FP32 and 16-bit kernels)
     T omega;                   // 1 / tau
     T fpref;                   // 1 - 1 / (2 tau)
     T eps, inv_eps, inv4eps;   // eps, 1/eps, 1/(4 eps)

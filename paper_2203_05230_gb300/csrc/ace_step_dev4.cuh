@@ -284,7 +284,7 @@ __device__ __forceinline__ void dev4_tile(const DevArgs<S>& d, const StepArgs<fl
             if (act) {
 #pragma unroll
                 for (int i = 0; i < 9; ++i) gout[(o + (unsigned)i * plane) >> 2] = make_uint2(packed[0][i], packed[1][i]);
-                *reinterpret_cast<float4*>(d.phout + o) = php;
+                st_policy(d.phout + o, php, l2_store_policy_all((a.l2_keep & L2_KEEP_PHI) != 0));
                 split_add2i(mai, mlo, make_float2(php.x, php.y));
                 split_add2i(mai, mlo, make_float2(php.z, php.w));
                 mmax = fmaxf(mmax, fmaxf(fmaxf(fabsf(php.x), fabsf(php.y)), fmaxf(fabsf(php.z), fabsf(php.w))));

@@ -203,7 +203,10 @@ __device__ __forceinline__ void pair_tile(const StepArgs<T>& a, const Vel& vel, 
                 V p2;
                 p2.x = pha;
                 p2.y = phb;
-                *reinterpret_cast<V*>(a.phi + o) = p2;
+                if constexpr (sizeof(T) == 4) // the phi plane's L2 policy (ace_kernels.cuh)
+                    st_policy(a.phi + o, p2, l2_store_policy_all((a.l2_keep & L2_KEEP_PHI) != 0));
+                else
+                    *reinterpret_cast<V*>(a.phi + o) = p2;
                 msum += (double)pha + (double)phb;
             }
         }

@@ -33,27 +33,11 @@ constexpr int Q32_STRIP = 128;            // columns of one warp
 constexpr int Q32_WARPS = Q32_THREADS / 32;
 constexpr int Q32_MIN_CTAS = 3;
 
-// The L2 policy of the f* stores: evict_last on a quarter of the lines when `keep`, else
-// the normal priority. With the alternating march a step first reads the rows the step
-// before wrote last; when the populations are of about the L2's size (measured on GB300:
-// 1536^2 to 2560^2), letting part of the written lines outlast the lines just read (dead
-// once read) turns more of those reads into L2 hits: 2048^2 went from 52.1 to 50.2 us
-// per step. Far above the L2's size (4096^2) the kept lines are the wrong ones and the
-// step is 3.5 % slower, so the host sets `keep` only in between.
-__device__ __forceinline__ unsigned long long q32_store_policy(bool keep)
-{
-    unsigned long long last, normal;
-    asm("createpolicy.fractional.L2::evict_last.b64 %0, 0.25;" : "=l"(last));
-    asm("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(normal));
-    return keep ? last : normal;
-}
-
-__device__ __forceinline__ void q32_store(float* p, float4 v, unsigned long long policy)
-{
-    asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1, %2, %3, %4}, %5;"
-                 :: "l"(p), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w), "l"(policy) : "memory");
-}
-
+// The f* stores carry an L2 policy (ace_kernels.cuh): with L2_KEEP_F, evict_last on a
+// quarter of the lines. With populations of about the L2's size (measured on GB300:
+// 1536^2 to 2560^2) this turns more of the next step's reads into L2 hits: 2048^2 went
+// from 52.1 to 51.0 us per step. Far above the L2's size (4096^2) the kept lines are the
+// wrong ones and the step is 3.5 % slower, so the host sets the bit only in between.
 struct Quad32Smem {
     float chi[Q32_WARPS][4][Q32_STRIP + 8]; // psi ring per warp: index j holds column x0 + j - 4
     float4 park[2][9][Q32_THREADS];        // pulled f of one row: [buffer][plane][thread] (nodes 0..3)
@@ -104,7 +88,7 @@ __device__ __forceinline__ double quad32_strip(const StepArgs<float>& a, const V
         float l1, l5, l8, r3, r6, r7; // xq - 1 (planes 1, 5, 8) and xq + 4 (3, 6, 7): edge lanes
     };
     Raw nxt;
-    const unsigned long long store_policy = q32_store_policy(a.l2_keep != 0);
+    const unsigned long long store_policy = l2_store_policy_quarter((a.l2_keep & L2_KEEP_F) != 0);
     float hv = 0.0f;
     float4 pp_next = make_float4(0.0f, 0.0f, 0.0f, 0.0f); // phi(t-1) of the row that collides next
     typename Vel::Row vr_next{};
@@ -247,9 +231,9 @@ __device__ __forceinline__ double quad32_strip(const StepArgs<float>& a, const V
             if (act) {
 #pragma unroll
                 for (int i = 0; i < 9; ++i)
-                    q32_store(a.fout + (o + (unsigned)i * plane), make_float4(o2[0][i].x, o2[0][i].y, o2[1][i].x, o2[1][i].y),
+                    st_policy(a.fout + (o + (unsigned)i * plane), make_float4(o2[0][i].x, o2[0][i].y, o2[1][i].x, o2[1][i].y),
                               store_policy);
-                *reinterpret_cast<float4*>(a.phi + o) = php;
+                st_policy(a.phi + o, php, l2_store_policy_all((a.l2_keep & L2_KEEP_PHI) != 0));
                 split_add2i(mai, mlo, make_float2(php.x, php.y));
                 split_add2i(mai, mlo, make_float2(php.z, php.w));
                 mmax = fmaxf(mmax, fmaxf(fmaxf(fabsf(php.x), fabsf(php.y)), fmaxf(fabsf(php.z), fabsf(php.w))));

@@ -167,7 +167,7 @@ struct lbm_ace_ctx {
     int rows = 0, grid_x = 0, grid_y = 0;
     int variant = 1;        // 1: ace_step (direct loads), 2: ace_step_bulk
     int dev4_ctas = 3;      // resident CTAs per SM the 16-bit quad kernel is compiled for
-    int l2_keep = 0;        // variant 8: f* stores keep part of their lines in L2 (StepArgs::l2_keep)
+    int l2_keep = 0;        // L2 priority bits of the stores (StepArgs::l2_keep)
     int tile_x = TILE_X;
     size_t smem = 0;        // dynamic shared memory of the chosen step kernel
     int* dev_err = nullptr; // set by a kernel whose bounded wait gave up (inside the result block)
@@ -900,14 +900,19 @@ static int init_impl(lbm_ace_ctx* c, const lbm_ace_params* p)
         c->variant = nx % 2 == 0 ? 4 : 1;
     // the deviation-storage kernels: four columns per thread when nx allows, else pairs
     if (is_dev(c)) c->variant = p->kernel_variant != 0 ? p->kernel_variant : (nx % 4 == 0 ? 7 : 5);
-    // the FP32 quad kernel keeps part of the f* it stores in L2 when one population
-    // buffer is between half and twice the L2's size (faster from 1536^2 to 2560^2 on
-    // GB300, slower far above; ace_step_quad.cuh)
-    if (c->variant == 8) {
+    // L2 priority of the stores (StepArgs::l2_keep, ace_kernels.cuh). The FP32 quad kernel
+    // keeps a quarter of the f* lines it stores when one population buffer is between
+    // half and twice the L2's size (faster from 1536^2 to 2560^2 on GB300, slower far
+    // above). The FP32 and 16-bit kernels keep the phi plane they store when it takes at
+    // most 0.6 of the L2 (4096^2: FP32 column pairs 204.5 -> 200.0 us, 16-bit quads
+    // 151.3 -> 150.0 us; 2048^2: 16-bit 42.6 -> 41.9 us).
+    {
         int l2 = 0;
         CK(c, cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, c->dev));
         const double fbytes = 9.0 * (double)n * (double)c->elem;
-        c->l2_keep = l2 > 0 && fbytes > 0.5 * l2 && fbytes <= 2.0 * l2;
+        c->l2_keep = 0;
+        if (c->variant == 8 && l2 > 0 && fbytes > 0.5 * l2 && fbytes <= 2.0 * l2) c->l2_keep |= L2_KEEP_F;
+        if (!is_f64(c) && l2 > 0 && 4.0 * (double)n <= 0.6 * l2) c->l2_keep |= L2_KEEP_PHI;
     }
 
     // launch shape of the fused step: one wave of resident CTAs when possible
