@@ -141,7 +141,9 @@ typedef struct lbm_ace_params {
                             The 16-bit deviation storage has two kernels of its own, also
                             bit-identical: 5 = two columns per thread (even nx), 7 = four
                             columns per thread (nx a multiple of 4); 0 picks 7 when it
-                            applies, else 5. */
+                            applies, else 5. The FP32 and 16-bit kernels give their
+                            stores L2 eviction priorities chosen from the lattice's size
+                            and the device's L2 size; they change timing, not results. */
 } lbm_ace_params;
 
 typedef struct lbm_ace_ctx lbm_ace_ctx; /* opaque; owns its device buffers */
