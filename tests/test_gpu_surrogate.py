@@ -224,6 +224,34 @@ def test_hybrid_with_accepted_windows_moves_time_and_keeps_mass(net):
         assert abs(a.mass() - m0) < 1e-5 * m0
 
 
+@pytest.mark.parametrize("prec", [A.F32, A.BF16DEV, A.F64])
+def test_hybrid_vortex_windows_equal_the_explicit_chain(net, prec):
+    """An accepted window is the velocity at its middle time followed by one forward: the
+    hybrid's field after four windows equals, bit for bit, that of the velocity kernel and
+    a forward call per window, and the lattice restarts from it at the same time."""
+    s = torch.cuda.current_stream()
+    net.set_params(W.surrogate_init_params(seed=3))
+    L, T, nw, K = 64, 640.0, 4, A.NET_K
+    phi0 = W.disk_phi0(L, L, 32.0, 44.0, 10.0, 1.0)
+    with A.vortex_lattice(L, T=T, precision=prec, phi0=phi0, stream=s.cuda_stream) as a, \
+         A.vortex_lattice(L, T=T, precision=prec, phi0=phi0, stream=s.cuda_stream) as b:
+        a.step(3)
+        b.step(3)
+        st = net.hybrid_advance(a, nw, mass_tol=1.0, width_tol=10.0)
+        assert st["surrogate_windows"] == nw and st["fallback_windows"] == 0
+        phi = torch.empty(L * L, device="cuda")
+        out, u, v = torch.empty_like(phi), torch.empty_like(phi), torch.empty_like(phi)
+        b.lbm_ace_get_phi_device(phi.data_ptr())
+        for j in range(nw):
+            b.lbm_ace_velocity_device(3 + j * K + 0.5 * K, u.data_ptr(), v.data_ptr())
+            net.forward(phi, u, v, out, 1, L, L)
+            phi, out = out, phi
+        b.lbm_ace_reset_device(phi.data_ptr(), 3 + nw * K)
+        b.synchronize()
+        assert a.t == b.t == 3 + nw * K
+        assert np.array_equal(a.phi(), b.phi())
+
+
 def test_hybrid_rejects_a_lattice_on_another_stream(net):
     other = torch.cuda.Stream()
     with field_lattice(32, 3, other) as a:
