@@ -52,7 +52,27 @@ ARITH_DTYPE = {"f64": "f64", "f32": "f32", "f16dev": "f32", "bf16dev": "f32"}
 # (an FMA-chain probe measured 1.256).
 F64_FLOP_PER_LUP = 204.0
 F64_PEAK_TFLOPS = 152 * 2.07e9 * 4 / 1e12
-L2_NOTE = "inputs larger than L2: 2 x 151 MB FP32 population buffers + 16.8 MB phi plane"
+L2_BYTES = 126e6  # GB300's L2 as the runtime reports it (cudaDevAttrL2CacheSize), about 126 MB
+
+
+def l2_note(L: int, precision: str) -> str:
+    """How the timed steps relate to the L2: the state's buffers and whether one population
+    buffer (what a step streams in) is larger than the L2."""
+    n = L * L
+    if precision in ("f32", "f64"):
+        e = 4 if precision == "f32" else 8
+        pop, parts = 9 * n * e, f"2 x {9 * n * e / 1e6:.1f} MB {precision.upper()} population buffers + " \
+                                 f"{n * e / 1e6:.1f} MB phi plane"
+        total = 19 * n * e
+    else:
+        pop, parts = 18 * n, f"2 x {18 * n / 1e6:.1f} MB 16-bit deviation buffers + 2 x {4 * n / 1e6:.1f} MB phi planes"
+        total = 44 * n
+    if pop > L2_BYTES:
+        return "inputs larger than L2: " + parts
+    if total <= L2_BYTES:
+        return f"state fits in L2 ({total / 1e6:.1f} MB: {parts}); no flush between steps: the L2-resident steady state"
+    return (f"state larger than L2 ({total / 1e6:.1f} MB: {parts}) but one population buffer smaller; no flush "
+            "between steps: part of a step's reads hit in L2")
 
 
 def parse():
@@ -88,8 +108,7 @@ def workload(args):
         "workload": f"single vortex {args.L}x{args.L} {args.precision.upper()} eps {v.eps} tau {v.tau} "
                     f"U0 {v.U0} T {v.T} steps, disk R {v.R:g} at ({v.xc:g}, {v.yc:g})",
         "lattice": [args.L, args.L], "T_period": v.T, "eps": v.eps, "tau": v.tau, "U0": v.U0,
-        "l2": L2_NOTE if args.precision in ("f32", "f64") else
-              "inputs larger than L2: 2 x 75.5 MB 16-bit deviation buffers + 2 x 16.8 MB phi planes",
+        "l2": l2_note(args.L, args.precision),
     }
 
 
