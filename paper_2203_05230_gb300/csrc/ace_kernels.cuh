@@ -43,7 +43,7 @@ constexpr int TILE_X = 128;
 // l2_keep): a policy from createpolicy rides on each st.global.L2::cache_hint. A step
 // reads first the rows the step before wrote last (alternating march), and what it reads
 // is dead once read, so letting written lines outlast read ones turns more of the next
-// step's reads into L2 hits where the data is of about the L2's size (measured on GB300).
+// step's reads into L2 hits where the kept data fits the L2 (measured on GB300).
 constexpr int L2_KEEP_F = 1, L2_KEEP_PHI = 2;
 
 // evict_last on `frac` of the lines when keep, else the normal priority (both policies
@@ -111,7 +111,7 @@ struct StepArgs {
     int first;                 // t == 0: no time-derivative term
     int tdir;                  // t & 1: march direction of the row bands (column-pair kernels)
     int l2_keep = 0;           // L2 priority of the stores (bits; 0 = normal): L2_KEEP_F = f* of
-                               // the FP32 quad kernel evict_last on a quarter of the lines,
+                               // the FP32 quad kernel evict_last on a quarter of the lines (unset),
                                // L2_KEEP_PHI = the phi plane evict_last (FP32 and 16-bit kernels)
     T omega;                   // 1 / tau
     T fpref;                   // 1 - 1 / (2 tau)

@@ -34,10 +34,10 @@ constexpr int Q32_WARPS = Q32_THREADS / 32;
 constexpr int Q32_MIN_CTAS = 3;
 
 // The f* stores carry an L2 policy (ace_kernels.cuh): with L2_KEEP_F, evict_last on a
-// quarter of the lines. With populations of about the L2's size (measured on GB300:
-// 1536^2 to 2560^2) this turns more of the next step's reads into L2 hits: 2048^2 went
-// from 52.1 to 51.0 us per step. Far above the L2's size (4096^2) the kept lines are the
-// wrong ones and the step is 3.5 % slower, so the host sets the bit only in between.
+// quarter of the lines. Alone it made more of the next step's reads L2 hits from 1536^2
+// to 2560^2 (2048^2: 52.1 -> 51.0 us per step), but keeping the phi plane (L2_KEEP_PHI)
+// pays more and the two compete for the same lines (2048^2: 47.8 us with phi alone, 49.9
+// with both), so the host leaves the bit unset and the f* stores get the normal priority.
 struct Quad32Smem {
     float chi[Q32_WARPS][4][Q32_STRIP + 8]; // psi ring per warp: index j holds column x0 + j - 4
     float4 park[2][9][Q32_THREADS];        // pulled f of one row: [buffer][plane][thread] (nodes 0..3)

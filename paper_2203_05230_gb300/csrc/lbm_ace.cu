@@ -900,18 +900,17 @@ static int init_impl(lbm_ace_ctx* c, const lbm_ace_params* p)
         c->variant = nx % 2 == 0 ? 4 : 1;
     // the deviation-storage kernels: four columns per thread when nx allows, else pairs
     if (is_dev(c)) c->variant = p->kernel_variant != 0 ? p->kernel_variant : (nx % 4 == 0 ? 7 : 5);
-    // L2 priority of the stores (StepArgs::l2_keep, ace_kernels.cuh). The FP32 quad kernel
-    // keeps a quarter of the f* lines it stores when one population buffer is between
-    // half and twice the L2's size (faster from 1536^2 to 2560^2 on GB300, slower far
-    // above). The FP32 and 16-bit kernels keep the phi plane they store when it takes at
-    // most 0.6 of the L2 (4096^2: FP32 column pairs 204.5 -> 200.0 us, 16-bit quads
-    // 151.3 -> 150.0 us; 2048^2: 16-bit 42.6 -> 41.9 us).
+    // L2 priority of the stores (StepArgs::l2_keep, ace_kernels.cuh): the FP32 and 16-bit
+    // kernels keep the phi plane they store when it takes at most 0.6 of the L2 (measured
+    // on GB300, us per step: FP32 quads at 2048^2 51.7 -> 47.8, FP32 column pairs at 4096^2
+    // 204.5 -> 200.0, 16-bit quads 151.3 -> 150.0 at 4096^2 and 42.6 -> 41.9 at 2048^2).
+    // L2_KEEP_F (a quarter of the f* lines) is not set: alone it helped from 1536^2 to
+    // 2560^2, but beside the kept phi plane it competes for the same lines and was slower
+    // (2048^2: 49.9 against 47.8 us; 2560^2: 80.2 against 74.3).
     {
         int l2 = 0;
         CK(c, cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, c->dev));
-        const double fbytes = 9.0 * (double)n * (double)c->elem;
         c->l2_keep = 0;
-        if (c->variant == 8 && l2 > 0 && fbytes > 0.5 * l2 && fbytes <= 2.0 * l2) c->l2_keep |= L2_KEEP_F;
         if (!is_f64(c) && l2 > 0 && 4.0 * (double)n <= 0.6 * l2) c->l2_keep |= L2_KEEP_PHI;
     }
 
