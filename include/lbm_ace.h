@@ -118,7 +118,9 @@ typedef struct lbm_ace_params {
                             LBM_ACE_F64 (whose phi is FP32), round to a finite FP32. Its
                             upload runs while the host prepares the velocity, without
                             waiting when phi0 is page-locked (cudaHostAlloc, cudaMallocHost,
-                            cudaHostRegister) */
+                            cudaHostRegister); from 2^20 nodes, FP64 and FP32 lattices
+                            upload it in row chunks on a second stream of the library's
+                            and initialise each chunk as it lands */
     double xc, yc, R;
     int device;          /* CUDA device ordinal */
     void* stream;        /* cudaStream_t for all device work; NULL = the legacy default stream */

@@ -82,6 +82,29 @@ cudaError_t device_pool(int dev, cudaMemPool_t* out)
     return cudaSuccess;
 }
 
+// A second stream per device (non-blocking), on which lattice creation uploads phi0 in row
+// chunks while the context's stream initialises the chunks already there; like the pool
+// it is made again when the device's context changes.
+cudaStream_t g_aux[kMaxDevices] = {};
+unsigned long long g_aux_ctx[kMaxDevices] = {};
+
+cudaError_t aux_stream(int dev, cudaStream_t* out)
+{
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    unsigned long long id = 0;
+    if (!current_ctx_id(&id)) return cudaErrorDeviceUninitialized;
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    if (!g_aux[dev] || g_aux_ctx[dev] != id) {
+        cudaStream_t st;
+        const cudaError_t e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return e;
+        g_aux[dev] = st;
+        g_aux_ctx[dev] = id;
+    }
+    *out = g_aux[dev];
+    return cudaSuccess;
+}
+
 // Mapped pinned host memory for the contexts' result blocks, in 128-byte slots (one
 // cache line each) cut from 4 KiB pages that are never freed: a cudaHostAlloc costs
 // about 80 us, more than a whole mass call. A page belongs to the CUDA context that was
@@ -168,6 +191,7 @@ struct lbm_ace_ctx {
     int variant = 1;        // 1: ace_step (direct loads), 2: ace_step_bulk
     int dev4_ctas = 3;      // resident CTAs per SM the 16-bit quad kernel is compiled for
     int l2_keep = 0;        // L2 priority bits of the stores (StepArgs::l2_keep)
+    cudaStream_t upload = nullptr; // the second stream while it may still copy into scratch (creation)
     int tile_x = TILE_X;
     size_t smem = 0;        // dynamic shared memory of the chosen step kernel
     int* dev_err = nullptr; // set by a kernel whose bounded wait gave up (inside the result block)
@@ -465,6 +489,55 @@ void launch_init_dev(lbm_ace_ctx* c, const double* dphi0, double t0)
     }
     default:
         ace_init_dev<S><<<g, 256, 0, c->stream>>>(dphi0, gs, phi, c->p.nx, c->p.ny, planes<float>(c));
+        break;
+    }
+}
+
+// The initial state of rows [y0, y1): the push of ace_init (f*_i(x - c_i) = f_i^eq(phi0(x),
+// u(x, 0)), phi plane = phi0) on those rows, the same arithmetic node for node, plus the
+// smallest index whose phi is not finite in the storage precision into *first_bad.
+// Rows are independent, so the upload of phi0 can be cut into row chunks that this
+// kernel initialises while the next chunk is still on its way.
+template <typename T, class Vel>
+__global__ void ace_init_rows(const double* __restrict__ phi0, T* __restrict__ fst, T* __restrict__ phi, int nx,
+                              int ny, int y0, int y1, Vel vel, unsigned long long* first_bad)
+{
+    const long long plane = (long long)nx * ny;
+    const long long k1 = (long long)y1 * nx;
+    for (long long k = (long long)y0 * nx + blockIdx.x * (long long)blockDim.x + threadIdx.x; k < k1;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(k % nx), y = (int)(k / nx);
+        const T ph = T(phi0[k]);
+        if (!isfinite(ph)) atomicMin(first_bad, (unsigned long long)k);
+        T u, v, up, vp, feq[9];
+        const typename Vel::Col cl = vel.col(x);
+        vel.at(cl, vel.rowv(cl, x, y), u, v, up, vp);
+        equilibrium(ph, u, v, feq);
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+            fst[i * plane + (long long)wrap_idx(y - cy_of(i), ny) * nx + wrap_idx(x - cx_of(i), nx)] = feq[i];
+        phi[k] = ph;
+    }
+}
+
+template <typename T>
+void launch_init_rows(lbm_ace_ctx* c, const double* dphi0, int y0, int y1, unsigned long long* first_bad)
+{
+    const int g = grid_for((long long)(y1 - y0) * c->p.nx, c->sms);
+    T* fst = (T*)c->f[c->cur];
+    T* phi = (T*)c->phi;
+    const int nx = c->p.nx, ny = c->p.ny;
+    switch (c->p.velocity_kind) {
+    case LBM_ACE_VEL_SINGLE_VORTEX:
+        ace_init_rows<T><<<g, 256, 0, c->stream>>>(dphi0, fst, phi, nx, ny, y0, y1, vortex<T>(c, 0.0), first_bad);
+        break;
+    case LBM_ACE_VEL_UNIFORM: {
+        VelUniform<T> v; v.ux = T(c->p.ux); v.uy = T(c->p.uy);
+        ace_init_rows<T><<<g, 256, 0, c->stream>>>(dphi0, fst, phi, nx, ny, y0, y1, v, first_bad);
+        break;
+    }
+    default:
+        ace_init_rows<T><<<g, 256, 0, c->stream>>>(dphi0, fst, phi, nx, ny, y0, y1, planes<T>(c), first_bad);
         break;
     }
 }
@@ -870,6 +943,7 @@ void lbm_ace_destroy(lbm_ace_ctx* c)
     if (!c) return;
     DeviceGuard g(c->dev);
     if (c->stream) cudaStreamSynchronize(c->stream); else cudaDeviceSynchronize();
+    if (c->upload) cudaStreamSynchronize(c->upload); // a creation that failed half-way
     for (void* b : {c->arena, static_cast<void*>(c->scratch)})
         if (b) cudaFreeAsync(b, c->stream); // back to the device's pool
     if (c->slot.host) release_slot(c->slot);
@@ -1000,10 +1074,35 @@ static int init_impl(lbm_ace_ctx* c, const lbm_ace_params* p)
     c->hres_dev = c->slot.dev;
 
     // initial phi first: its upload (asynchronous from page-locked memory) runs while the
-    // host computes the velocity tables below
+    // host computes the velocity tables below. For a large FP64 or FP32 lattice it goes in
+    // kChunks row chunks on a second stream, each followed by an event on which the
+    // context's stream waits before it initialises that chunk, so the init kernel works
+    // under the upload of the next chunk (the 16-bit init reads phi0 around each node and
+    // takes it whole).
     rc = ensure_scratch(c, n);
     if (rc) return rc;
-    if (p->phi0) CK(c, cudaMemcpyAsync(c->scratch, p->phi0, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    constexpr int kChunks = 4;
+    const bool chunked = p->phi0 && !is_dev(c) && n >= (size_t(1) << 20) && ny >= kChunks;
+    struct Events { // released on every return
+        cudaEvent_t e[kChunks + 1] = {};
+        ~Events() { for (cudaEvent_t x : e) if (x) cudaEventDestroy(x); }
+    } ev;
+    auto chunk_row = [&](int k) { return (int)((long long)ny * k / kChunks); };
+    if (chunked) {
+        cudaStream_t aux;
+        CK(c, aux_stream(c->dev, &aux));
+        for (cudaEvent_t& x : ev.e) CK(c, cudaEventCreateWithFlags(&x, cudaEventDisableTiming));
+        CK(c, cudaEventRecord(ev.e[0], c->stream)); // the scratch buffer is allocated on c->stream
+        CK(c, cudaStreamWaitEvent(aux, ev.e[0], 0));
+        c->upload = aux;
+        for (int k = 0; k < kChunks; ++k) {
+            const size_t o = (size_t)chunk_row(k) * nx, m = (size_t)(chunk_row(k + 1) - chunk_row(k)) * nx;
+            CK(c, cudaMemcpyAsync(c->scratch + o, p->phi0 + o, m * sizeof(double), cudaMemcpyHostToDevice, aux));
+            CK(c, cudaEventRecord(ev.e[k + 1], aux));
+        }
+    } else if (p->phi0) {
+        CK(c, cudaMemcpyAsync(c->scratch, p->phi0, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    }
 
     // velocity
     if (p->velocity_kind == LBM_ACE_VEL_SINGLE_VORTEX) {
@@ -1058,6 +1157,26 @@ static int init_impl(lbm_ace_ctx* c, const lbm_ace_params* p)
     c->cur = 0;
     c->t = 0;
     c->pcur = 0;
+    if (chunked) { // each chunk once its rows are on the device; phi0 checked on the way
+        unsigned long long* first_bad = reinterpret_cast<unsigned long long*>(c->result + 1);
+        CK(c, cudaMemsetAsync(first_bad, 0xff, sizeof(unsigned long long), c->stream));
+        for (int k = 0; k < kChunks; ++k) {
+            CK(c, cudaStreamWaitEvent(c->stream, ev.e[k + 1], 0));
+            if (is_f64(c)) launch_init_rows<double>(c, src, chunk_row(k), chunk_row(k + 1), first_bad);
+            else launch_init_rows<float>(c, src, chunk_row(k), chunk_row(k + 1), first_bad);
+        }
+        c->fresh = true;
+        CK(c, cudaGetLastError());
+        unsigned long long* hbad = reinterpret_cast<unsigned long long*>(c->hres + 4);
+        CK(c, cudaMemcpyAsync(hbad, first_bad, sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
+        CK(c, cudaMemsetAsync(first_bad, 0, sizeof(unsigned long long), c->stream));
+        CK(c, cudaStreamSynchronize(c->stream));
+        c->upload = nullptr; // the stream waited for every chunk's copy
+        const unsigned long long bad = *hbad;
+        if (bad != ~0ULL)
+            return fail(c, LBM_ACE_EINVAL, is_f64(c) ? "phi0[%llu] is not finite" : "phi0[%llu] is not finite as FP32", bad);
+        return LBM_ACE_OK;
+    }
     switch (p->precision) {
     case LBM_ACE_F64: launch_init_t<double>(c, src, 0.0); break;
     case LBM_ACE_F32: launch_init_t<float>(c, src, 0.0); break;

@@ -92,3 +92,41 @@ def test_phi0_beyond_fp32_range_is_rejected_for_fp32_storage(pin, precision):
     with A.Lattice(nx=300, ny=300, phi0=src, precision=precision) as g:
         assert g.lbm_ace_steps_done() == 0
     del keep
+
+
+@pytest.mark.parametrize("precision", [A.F32, A.F64])
+@pytest.mark.parametrize("pin", [True, False])
+def test_chunked_creation_equals_the_whole_upload(precision, pin):
+    """From 2^20 nodes, FP64 and FP32 lattices upload phi0 in row chunks on a second
+    stream and initialise each chunk as it lands. The state must equal, bit for bit, the
+    one the whole-plane init gives (reached here through a restart at t = 0 from the same
+    values, which FP32 holds exactly)."""
+    L = 1024
+    phi0 = W.random_smooth_phi(L, L, seed=11).astype(np.float32).astype(np.float64)
+    keep, src = pinned_like(phi0) if pin else (None, phi0)
+    with A.Lattice(nx=L, ny=L, precision=precision, phi0=src, T_period=16384.0) as a, \
+         A.Lattice(nx=L, ny=L, precision=precision, T_period=16384.0) as b:
+        b.lbm_ace_reset_device(torch.tensor(phi0.astype(np.float32), device="cuda").data_ptr(), 0)
+        b.synchronize()
+        fa, pa = a.get_state()
+        fb, pb = b.get_state()
+        assert np.array_equal(fa, fb) and np.array_equal(pa, pb)
+        a.step(3)
+        b.step(3)
+        assert np.array_equal(a.phi(), b.phi())
+    del keep
+
+
+@pytest.mark.parametrize("k", [7, 1024 * 1000 + 5])
+def test_chunked_creation_rejects_non_finite_phi0(k):
+    phi0 = np.full((1024, 1024), 0.5)
+    phi0.flat[k] = np.nan
+    phi0.flat[1024 * 1023] = np.inf
+    keep, src = pinned_like(phi0)
+    with pytest.raises(A.LbmAceError) as e:
+        A.Lattice(nx=1024, ny=1024, phi0=src, precision=A.F32)
+    assert e.value.status == A.EINVAL and f"phi0[{k}]" in str(e.value)
+    with A.Lattice(nx=1024, ny=1024, phi0=np.full((1024, 1024), 0.5), precision=A.F32) as g:
+        g.step(2)
+        assert g.mass() == pytest.approx(0.5 * 1024 * 1024, rel=1e-6)
+    del keep
