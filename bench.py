@@ -471,7 +471,7 @@ def forms_record(args, stream):
 def run_e2e(args, v, prec, stream, dev, A, ws=1, runs=3):
     """The same metric through the public API with host buffers: phi0 uploaded from
     pinned host memory, K steps, phi and the mass read back; wall clock. A run is about
-    2 ms of host and device work, so host noise moves one sample by several per cent: the
+    1.5 ms of host and device work, so host noise moves one sample by several per cent: the
     value is the median of `runs` complete runs (each creates, steps, reads back and
     destroys its own lattice), all listed. With ws > 1 ranks, each run's time is the
     slowest rank's and the value is whole-job."""
