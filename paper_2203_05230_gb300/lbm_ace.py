@@ -269,6 +269,9 @@ class Lattice:
     step = lbm_ace_step
 
     def lbm_ace_get_phi(self, out: Optional[np.ndarray] = None) -> np.ndarray:
+        """phi(x, t) as float64 [ny, nx], into `out` when given (C-contiguous float64 of
+        nx * ny values). A page-locked `out`, such as the numpy view of a pinned torch
+        tensor, is written by the library's kernel directly; other memory through a copy."""
         if out is None:
             out = np.empty((self.ny, self.nx), dtype=np.float64)
         assert out.dtype == np.float64 and out.flags.c_contiguous and out.size == self.nx * self.ny
